@@ -1,0 +1,210 @@
+"""Seeded synthetic initial data for the compact GKS (numpy only).
+
+Holds none of the scheme's arithmetic: it only builds cell averages ``W`` and
+cell-averaged gradients ``G`` of initial conditions shaped like the paper's
+test families (Sec. 6): advected density sine waves (Sec. 6.1, Sec. 6.10),
+two-state Riemann problems (Sec. 6.5), four-quadrant Riemann problems, smooth
+density modes crossed by planar shocks (shock/smooth-wave interaction,
+Sec. 6.3) and a solenoidal turbulence-like velocity field (Sec. 6.13).
+Both the CUDA library's tests and the oracle's tests take their inputs here.
+
+Layouts: ``W[v][k][j][i]`` with v = rho, rho u (, rho v, rho w), rho E;
+``G[d][v][k][j][i]`` = d W / d x_d.  Arrays are returned squeezed to the
+dimension (1D: (nv, n) and (1, nv, n)).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def _cons(rho, vel, p, gamma):
+    """Pointwise conservative variables from primitives; vel is a list of arrays."""
+    ke = sum(u * u for u in vel)
+    out = [rho] + [rho * u for u in vel] + [p / (gamma - 1.0) + 0.5 * rho * ke]
+    return np.stack(out)
+
+
+def sine_wave(dim: int, n: int, t: float = 0.0, gamma: float = GAMMA, amp: float = 0.2, L: float = 2.0):
+    """rho = 1 + amp sin(pi (x + y + z - dim t)), U = 1 per axis, p = 1 on [0, L]^dim (Sec. 6.1, 6.10).
+
+    Exact cell averages (sinc factor) and exact averaged gradients (face
+    averages differenced, Gauss theorem).  Returns (W, G, h).
+    """
+    h = L / n
+    c = (np.arange(n) + 0.5) * h
+    grids = np.meshgrid(*([c] * dim), indexing="ij")[::-1]  # grids[a] varies along axis a in [k][j][i] order
+    shape = (n,) * dim
+    s = math.sin(math.pi * h / 2) / (math.pi * h / 2)
+    phase = sum(grids) - dim * t
+    rho_avg = 1.0 + amp * np.sin(math.pi * phase) * s**dim
+    nv = dim + 2
+    W = np.empty((nv,) + shape)
+    W[0] = rho_avg
+    for a in range(dim):
+        W[1 + a] = rho_avg
+    W[dim + 1] = 1.0 / (gamma - 1.0) + 0.5 * dim * rho_avg
+    G = np.zeros((dim, nv) + shape)
+    drho = amp * s ** (dim - 1) * (np.sin(math.pi * (phase + h / 2)) - np.sin(math.pi * (phase - h / 2))) / h
+    for d in range(dim):
+        G[d, 0] = drho
+        for a in range(dim):
+            G[d, 1 + a] = drho
+        G[d, dim + 1] = 0.5 * dim * drho
+    return W, G, h
+
+
+def sine_exact_rho(dim: int, n: int, t: float, amp: float = 0.2, L: float = 2.0):
+    W, _, _ = sine_wave(dim, n, t=t, amp=amp, L=L)
+    return W[0]
+
+
+def riemann_1d(n: int, seed: int, gamma: float = GAMMA):
+    """Two seeded states, rho, p ~ U[0.1, 1], u ~ U[-0.5, 0.5], jump at x = 0.5 on [0, 1]."""
+    rng = np.random.default_rng(seed)
+    st = [(rng.uniform(0.1, 1.0), rng.uniform(-0.5, 0.5), rng.uniform(0.1, 1.0)) for _ in range(2)]
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    left = x < 0.5
+    rho = np.where(left, st[0][0], st[1][0])
+    u = np.where(left, st[0][1], st[1][1])
+    p = np.where(left, st[0][2], st[1][2])
+    W = _cons(rho, [u], p, gamma)
+    G = np.zeros((1,) + W.shape)
+    return W, G, h, st
+
+
+def quadrants_2d(n: int, seed: int, gamma: float = GAMMA, nx: int | None = None):
+    """Four seeded quadrant states on [0, 1]^2 split at 0.5: rho, p ~ U[0.1, 1.5], u, v ~ U[-0.8, 0.8].
+
+    Piecewise constant, so the cell-averaged gradients are zero.  ``nx`` allows
+    a non-square grid (same h, domain [0, nx h] x [0, 1]).
+    """
+    rng = np.random.default_rng(seed)
+    nx = n if nx is None else nx
+    st = [(rng.uniform(0.1, 1.5), rng.uniform(-0.8, 0.8), rng.uniform(-0.8, 0.8), rng.uniform(0.1, 1.5)) for _ in range(4)]
+    h = 1.0 / n
+    x = (np.arange(nx) + 0.5) * h
+    y = (np.arange(n) + 0.5) * h
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    q = (X >= 0.5 * nx * h).astype(int) + 2 * (Y >= 0.5).astype(int)
+    arr = np.array(st)
+    rho, u, v, p = (arr[q, i] for i in range(4))
+    W = _cons(rho, [u, v], p, gamma)
+    G = np.zeros((2,) + W.shape)
+    return W, G, h
+
+
+def _fourier_shock_point(X, Y, modes, shocks, gamma):
+    rho = np.ones_like(X)
+    for (kx, ky, ph) in modes:
+        rho = rho + 0.2 / len(modes) * np.cos(2 * math.pi * (kx * X + ky * Y) + ph)
+    u = np.zeros_like(X)
+    v = np.zeros_like(X)
+    p = np.ones_like(X)
+    for (nx_, ny_, off, M) in shocks:
+        nn = math.hypot(nx_, ny_)
+        s = np.mod(nx_ * X + ny_ * Y - off, 1.0)
+        behind = s > 1.0 - 0.125 * nn
+        c = np.sqrt(gamma * p / rho)
+        r = (gamma + 1) * M * M / ((gamma - 1) * M * M + 2)
+        pr = 1 + 2 * gamma / (gamma + 1) * (M * M - 1)
+        du = M * c * (1 - 1 / r)
+        rho = np.where(behind, rho * r, rho)
+        p = np.where(behind, p * pr, p)
+        u = np.where(behind, u + du * nx_ / nn, u)
+        v = np.where(behind, v + du * ny_ / nn, v)
+    return rho, u, v, p
+
+
+def fourier_shocks_2d(n: int, seed: int, gamma: float = GAMMA, sub: int = 8):
+    """Periodic [0,1]^2: rho = 1 + 0.2/16 sum_m cos(2 pi k_m.x + phi_m), 1 <= |k_m|_inf <= 8,
+    u = 0, p = 1, then four planar shocks (normals from {(1,0),(0,1),(1,1),(1,-1)},
+    offset ~ U[0,1), Mach ~ U[1.5, 3]); each shock sets the Rankine-Hugoniot
+    post-shock state of the local gas in a slab of width 0.125 behind its front.
+    Averages by sub x sub sampling, gradients by the Gauss theorem with sub
+    samples per face.
+    """
+    rng = np.random.default_rng(seed)
+    modes = []
+    while len(modes) < 16:
+        kx, ky = rng.integers(-8, 9, size=2)
+        if max(abs(kx), abs(ky)) >= 1:
+            modes.append((int(kx), int(ky), rng.uniform(0, 2 * math.pi)))
+    normals = [(1, 0), (0, 1), (1, 1), (1, -1)]
+    shocks = []
+    for i in range(4):
+        nrm = normals[rng.integers(0, 4)]
+        shocks.append((nrm[0], nrm[1], rng.uniform(0, 1), rng.uniform(1.5, 3.0)))
+    h = 1.0 / n
+    nv = 4
+    W = np.zeros((nv, n, n))
+    G = np.zeros((2, nv, n, n))
+    off = (np.arange(sub) + 0.5) / sub - 0.5
+    base = (np.arange(n) + 0.5) * h
+    # averages: midpoint rule on sub x sub sub-cells, accumulated row by row to bound memory
+    for a in range(sub):
+        for b in range(sub):
+            Y, X = np.meshgrid(base + off[a] * h, base + off[b] * h, indexing="ij")
+            rho, u, v, p = _fourier_shock_point(X, Y, modes, shocks, gamma)
+            W += _cons(rho, [u, v], p, gamma)
+    W /= sub * sub
+    # gradients: Gauss theorem with sub samples on each face
+    for a in range(sub):
+        for side, sgn in ((0.5, 1.0), (-0.5, -1.0)):
+            Y, X = np.meshgrid(base + off[a] * h, base + side * h, indexing="ij")
+            rho, u, v, p = _fourier_shock_point(X, Y, modes, shocks, gamma)
+            G[0] += sgn * _cons(rho, [u, v], p, gamma)
+            Y, X = np.meshgrid(base + side * h, base + off[a] * h, indexing="ij")
+            rho, u, v, p = _fourier_shock_point(X, Y, modes, shocks, gamma)
+            G[1] += sgn * _cons(rho, [u, v], p, gamma)
+    G /= sub * h
+    return W, G, h
+
+
+def batch_sizes(count: int, seed: int, lo: int = 64, hi: int = 1024):
+    """Grid sides drawn log-uniformly in [lo, hi], rounded to even."""
+    rng = np.random.default_rng(seed)
+    s = np.exp(rng.uniform(math.log(lo), math.log(hi), size=count))
+    return [int(max(2, 2 * round(x / 2))) for x in s]
+
+
+def turbulence_3d(n: int, seed: int, gamma: float = GAMMA, mach: float = 0.6, k0: float = 4.0):
+    """Periodic [0,1]^3, rho = 1, solenoidal random-phase velocity with
+    E(k) ~ k^4 exp(-2 (k/k0)^2), scaled to u_rms = 1, p = 1/(gamma mach^2).
+
+    Averages are the point values at cell centres, gradients spectral
+    derivatives there (synthetic input, not a discretisation claim).
+    """
+    rng = np.random.default_rng(seed)
+    k1 = np.fft.fftfreq(n, d=1.0 / n)
+    KZ, KY, KX = np.meshgrid(k1, k1, k1, indexing="ij")
+    kk = np.sqrt(KX**2 + KY**2 + KZ**2)
+    kk[0, 0, 0] = 1.0
+    amp = np.sqrt(kk**4 * np.exp(-2 * (kk / k0) ** 2) / (4 * math.pi * kk**2))
+    amp[0, 0, 0] = 0.0
+    comps = []
+    for _ in range(3):
+        ph = rng.uniform(0, 2 * math.pi, size=kk.shape)
+        comps.append(amp * np.exp(1j * ph))
+    # project out the component along k
+    dot = (comps[0] * KX + comps[1] * KY + comps[2] * KZ) / kk**2
+    comps = [comps[0] - dot * KX, comps[1] - dot * KY, comps[2] - dot * KZ]
+    vel = [np.real(np.fft.ifftn(c)) for c in comps]
+    urms = math.sqrt(sum(float(np.mean(v * v)) for v in vel) / 3.0)
+    vel = [v / urms for v in vel]
+    dvel = []
+    for c in comps:
+        dvel.append([np.real(np.fft.ifftn(1j * 2 * math.pi * K * c)) / urms for K in (KX, KY, KZ)])
+    rho = np.ones((n, n, n))
+    p = np.full((n, n, n), 1.0 / (gamma * mach * mach))
+    W = _cons(rho, vel, p, gamma)
+    G = np.zeros((3, 5, n, n, n))
+    for d in range(3):
+        for a in range(3):
+            G[d, 1 + a] = dvel[a][d]
+        G[d, 4] = sum(vel[a] * dvel[a][d] for a in range(3))
+    return W, G, 1.0 / n

@@ -1,0 +1,221 @@
+"""Scheme-level pins of the oracle (no GPU).
+
+P3  GENO preserves the linear scheme on smooth waves (Sec. 3.1, linearity
+    preserving): results equal the chi = 1 run to round-off; on a jump they
+    differ (the pin is not vacuous).
+P4  design order on the advected density sine wave (Sec. 6.1, Sec. 6.10):
+    eighth order in 1D with dt ~ h^3 (so the time error is below the spatial
+    one), fourth order in 2D with dt ~ h^2.
+P5  conservation: with periodic boundaries the sums of the cell averages are
+    constant (Eq. semifvs, telescoping fluxes); the sums of the cell-averaged
+    gradients vanish (Eq. slope, telescoping interface states).
+P8  symmetries: mirror x -> -x, transposition x <-> y, and invariance of
+    y-independent data.
+P9  convergence to the exact Riemann solution of seeded two-state problems.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2507_20461_gb300 import inputs as I
+
+
+def _run(oracle, cfg, W, G, dt, nsteps):
+    W = np.ascontiguousarray(W, dtype=np.float64).copy()
+    G = np.ascontiguousarray(G, dtype=np.float64).copy()
+    for _ in range(nsteps):
+        r = oracle.step(cfg, dt, W, G)
+        assert r == 0, r
+    return W, G
+
+
+def test_geno_equals_linear_on_smooth_1d(oracle):
+    W, G, h = I.sine_wave(1, 32)
+    res = []
+    for lim in (0, 1):
+        cfg = oracle.make_cfg(1, (32,), h, limiter=lim)
+        res.append(_run(oracle, cfg, W, G, 0.2 * h, 10))
+    assert np.max(np.abs(res[0][0] - res[1][0])) < 1e-13
+    assert np.max(np.abs(res[0][1] - res[1][1])) < 1e-11
+
+
+def test_geno_equals_linear_on_smooth_2d(oracle):
+    W, G, h = I.sine_wave(2, 12)
+    res = []
+    for lim in (0, 1):
+        cfg = oracle.make_cfg(2, (12, 12), h, limiter=lim)
+        res.append(_run(oracle, cfg, W, G, 0.2 * h, 3))
+    assert np.max(np.abs(res[0][0] - res[1][0])) < 1e-13
+
+
+def test_geno_differs_from_linear_on_jump(oracle):
+    W, G, h, _ = I.riemann_1d(32, seed=1)
+    res = []
+    for lim in (0, 1):
+        cfg = oracle.make_cfg(1, (32,), h, bc=1, limiter=lim)
+        res.append(_run(oracle, cfg, W, G, 0.02 * h, 3))
+    assert np.max(np.abs(res[0][0] - res[1][0])) > 1e-6
+
+
+def _order_run(oracle, dim, n, dt_fn, T):
+    W, G, h = I.sine_wave(dim, n)
+    cfg = oracle.make_cfg(dim, (n,) * dim, h)
+    nst = int(math.ceil(T / dt_fn(h)))
+    W, G = _run(oracle, cfg, W, G, T / nst, nst)
+    return float(np.mean(np.abs(W[0] - I.sine_exact_rho(dim, n, T))))
+
+
+def test_design_order_1d(oracle):
+    """E1 of Sec. 6.1 (rho = 1 + 0.2 sin(pi x), U = p = 1 on [0, 2], periodic)."""
+    e = [_order_run(oracle, 1, n, lambda h: 0.2 * h**3, 0.05) for n in (8, 16, 32)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert orders[-1] >= 7.5, (e, orders)
+
+
+def test_design_order_2d(oracle):
+    """Cartesian counterpart of the accuracy test of Sec. 6.10 in 2D."""
+    e = [_order_run(oracle, 2, n, lambda h: 0.1 * h**2, 0.1) for n in (8, 16)]
+    order = math.log2(e[0] / e[1])
+    assert order >= 3.6, (e, order)
+
+
+def test_design_order_3d(oracle):
+    e = [_order_run(oracle, 3, n, lambda h: 0.1 * h**2, 0.05) for n in (4, 8)]
+    order = math.log2(e[0] / e[1])
+    assert order >= 3.6, (e, order)
+
+
+@pytest.mark.parametrize("dim,n", [(1, 24), (2, 10), (3, 5)])
+def test_conservation_periodic(oracle, dim, n):
+    rng = np.random.default_rng(dim)
+    W, G, h = I.sine_wave(dim, n)
+    # perturb to a generic smooth-ish state
+    W = W * (1 + 0.05 * rng.random(W.shape))
+    G = G + 0.1 * rng.normal(size=G.shape)
+    cfg = oracle.make_cfg(dim, (n,) * dim, h)
+    s0 = W.reshape(dim + 2, -1).sum(axis=1)
+    W1, G1 = _run(oracle, cfg, W, G, 0.1 * h, 4)
+    s1 = W1.reshape(dim + 2, -1).sum(axis=1)
+    np.testing.assert_allclose(s1, s0, rtol=1e-13)
+    gs = G1.reshape(dim, dim + 2, -1).sum(axis=2)
+    np.testing.assert_allclose(gs, 0.0, atol=1e-10 * np.abs(G1).max() * G1[0, 0].size)
+
+
+def test_mirror_symmetry_1d(oracle):
+    n = 40
+    W, G, h, _ = I.riemann_1d(n, seed=3)
+    W = W + 0.01 * np.sin(np.arange(n))[None, :]
+    cfg = oracle.make_cfg(1, (n,), h, bc=1)
+
+    def mirror(W, G):
+        Wm = W[:, ::-1].copy()
+        Wm[1] *= -1
+        Gm = -G[:, :, ::-1].copy()
+        Gm[:, 1] *= -1
+        return Wm, Gm
+
+    W1, G1 = _run(oracle, cfg, W, G, 0.05 * h, 3)
+    Wm, Gm = mirror(W, G)
+    W2, G2 = _run(oracle, cfg, Wm, Gm, 0.05 * h, 3)
+    W2b, G2b = mirror(W2, G2)
+    np.testing.assert_allclose(W2b, W1, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(G2b, G1, rtol=1e-11, atol=1e-11)
+
+
+def test_transpose_symmetry_2d(oracle):
+    n = 10
+    W, G, h = I.quadrants_2d(n, seed=4)
+    rng = np.random.default_rng(4)
+    W = W * (1 + 0.02 * rng.random(W.shape))
+    cfg = oracle.make_cfg(2, (n, n), h, bc=1)
+
+    def transpose(W, G):
+        Wt = np.transpose(W, (0, 2, 1)).copy()
+        Wt[[1, 2]] = Wt[[2, 1]]
+        Gt = np.transpose(G, (0, 1, 3, 2)).copy()
+        Gt = Gt[[1, 0]]
+        Gt[:, [1, 2]] = Gt[:, [2, 1]]
+        return Wt, Gt
+
+    W1, G1 = _run(oracle, cfg, W, G, 0.05 * h, 2)
+    Wt, Gt = transpose(W, G)
+    W2, G2 = _run(oracle, cfg, Wt, Gt, 0.05 * h, 2)
+    W2b, G2b = transpose(W2, G2)
+    np.testing.assert_allclose(W2b, W1, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(G2b, G1, rtol=1e-10, atol=1e-10)
+
+
+def test_y_invariant_stays_y_invariant(oracle):
+    n1, ny = 24, 6
+    W1d, G1d, h, _ = I.riemann_1d(n1, seed=5)
+    W = np.zeros((4, ny, n1))
+    W[0] = W1d[0]
+    W[1] = W1d[1]
+    W[3] = W1d[2]
+    G = np.zeros((2, 4, ny, n1))
+    cfg = oracle.make_cfg(2, (n1, ny), h, bc=0)
+    W, G = _run(oracle, cfg, W, G, 0.05 * h, 2)
+    assert np.max(np.abs(W - W[:, :1, :])) < 1e-13
+    assert np.max(np.abs(W[2])) < 1e-13
+    assert np.max(np.abs(G[1])) < 1e-11
+
+
+def test_converges_to_exact_riemann(oracle):
+    """Seeded two-state problems of the config-1 family (rho, p ~ U[0.1, 1],
+    u ~ U[-0.5, 0.5], transmissive ends, run until the fastest wave is 0.43
+    from the centre).  L1 density distance to the exact solution (cell
+    averages by 64-point sampling): for every seed the N = 256 error is below
+    the N = 32 error, and the median rate over seeds is >= 0.45.  (Convergence
+    is slow for some seeds: post-shock noise, which the temporal limiting at
+    strong discontinuities that the paper defers to earlier work would damp.)"""
+    from oracle import riemann
+
+    rates = []
+    for seed in range(6):
+        errs = []
+        for n in (32, 256):
+            W, G, h, st = I.riemann_1d(n, seed)
+            cfg = oracle.make_cfg(1, (n,), h, bc=1)
+            t = 0.45 / oracle.max_wavespeed(cfg, W) / 1.05
+            tt = 0.0
+            W = W.copy()
+            G = G.copy()
+            while tt < t - 1e-14:
+                dt = min(0.4 * h / oracle.max_wavespeed(cfg, W), t - tt)
+                assert oracle.step(cfg, dt, W, G) == 0
+                tt += dt
+            ex = riemann.cell_averages(st[0], st[1], n, t)
+            errs.append(float(np.mean(np.abs(W[0] - ex[0]))))
+        assert errs[1] < errs[0], (seed, errs)
+        rates.append(math.log2(errs[0] / errs[1]) / 3)
+    assert float(np.median(rates)) >= 0.45, rates
+
+
+def _contact_overshoot(oracle, limiter):
+    n = 64
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    rho = np.where(x < 0.5, 1.0, 0.5)
+    u = 0.5 * np.ones(n)
+    p = np.ones(n)
+    W = np.stack([rho, rho * u, p / 0.4 + 0.5 * rho * u * u])
+    G = np.zeros((1, 3, n))
+    cfg = oracle.make_cfg(1, (n,), h, bc=1, limiter=limiter)
+    worst = 0.0
+    for _ in range(40):
+        dt = 0.4 * h / oracle.max_wavespeed(cfg, W)
+        assert oracle.step(cfg, dt, W, G) == 0
+        worst = max(worst, W[0].max() - 1.0, 0.5 - W[0].min())
+    return worst
+
+
+def test_contact_overshoot_below_linear(oracle):
+    """An isolated contact (u = 0.5, p = 1, rho 1 | 0.5): GENO keeps the density
+    overshoot under half of the linear scheme's and under 3% of the data.
+    (Component-wise blending of conservative variables perturbs the pressure at
+    a contact, so GENO is essentially, not strictly, non-oscillatory here.)"""
+    geno = _contact_overshoot(oracle, 0)
+    lin = _contact_overshoot(oracle, 1)
+    assert geno <= 0.5 * lin, (geno, lin)
+    assert geno <= 0.03, geno
