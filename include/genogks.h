@@ -1,0 +1,196 @@
+/*
+ * genogks.h - C ABI of the GB300 (sm_103a) compact gas-kinetic scheme with
+ * GENO reconstruction (Zhao & Xu, arXiv 2507.20461).
+ *
+ * The library advances cell averages W and cell-averaged gradients grad W of
+ * the Euler equations on uniform 1D/2D/3D Cartesian grids:
+ *   - reconstruction (Sec. 3, Sec. 4.2, Sec. 4.3): GENO, R = chi q^H +
+ *     (1 - chi) q^L (Eq. HLP) with the path function chi = tanh(C alpha) /
+ *     tanh(C) (Eq. HLP-weight) and the ultimate smoothness indicator alpha
+ *     (Eq. HLP-sp); q^H is the compact high-order linear polynomial from the
+ *     averages and averaged gradients of the face neighbours (p^7 in 1D,
+ *     Eq. 8th-compact-HLP; a least-squares cubic on Cartesian cells in 2D/3D,
+ *     Eq. 6th-compact-HLP), q^L the ENO-type combination of sub-stencil
+ *     polynomials (Eq. HLP-q-loworder);
+ *   - flux (Sec. 2): the time-dependent gas-kinetic (BGK) distribution at
+ *     every face Gauss point, integrated in time;
+ *   - update (Sec. 2, Eq. semifvs, Eq. slope): two-stage fourth-order time
+ *     stepping of the averages, and the averaged gradients from the interface
+ *     states by the Gauss theorem.
+ * The paper defers the flux and the time stepping to earlier work; the
+ * formulations used are stated beside each entry point.
+ *
+ * Conventions for every call:
+ *   - Layouts are row-major with x fastest.  W[v][k][j][i] holds the nv =
+ *     dim + 2 conservative variables (rho, rho u, [rho v, [rho w]], rho E);
+ *     G[d][v][k][j][i] holds dW_v/dx_d in physical units.  No ghost cells.
+ *   - Faces of direction d have extent n_d + 1 along d and n_e across; face
+ *     arrays list all x faces, then y faces, then z faces (F faces in total,
+ *     see gks_face_count).  Face (i,j,k) of direction d lies between cell
+ *     (i,j,k) - e_d (its "minus" side) and cell (i,j,k) (its "plus" side).
+ *   - Gauss points per face: 1 (1D); 2 (2D) at tangential coordinates
+ *     -/+ h/(2 sqrt 3); 4 (3D) as g = a + 2 b, a for the lower tangential axis.
+ *   - Pointers are borrowed for the duration of the call.  A pointer flagged
+ *     on_device must be device memory of the handle's device; otherwise it is
+ *     host memory.  The library owns every buffer it allocates.
+ *   - All device work is ordered on the handle's stream (gks_opts_t.stream).
+ *     gks_step and gks_step_cfl return before the work finishes; errors of
+ *     that work (the status word) are reported by the next synchronising call
+ *     (gks_get_state, gks_status, gks_max_wavespeed).
+ *   - Return value: GKS_OK (0) or a negative GKS_ERR_* code; gks_last_error
+ *     gives a message.  No call aborts the process; no call falls back to the
+ *     CPU.
+ */
+#ifndef GENOGKS_H
+#define GENOGKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GKS_OK 0
+#define GKS_ERR_ARG (-1)         /* invalid argument                                        */
+#define GKS_ERR_CUDA (-2)        /* a CUDA call failed (message in gks_last_error)           */
+#define GKS_ERR_OOM (-3)         /* device allocation failed or workspace too small          */
+#define GKS_ERR_NONPHYSICAL (-4) /* rho <= 0, p <= 0 or a non-finite value was produced      */
+#define GKS_ERR_TIMEOUT (-5)     /* a bounded device wait gave up                            */
+#define GKS_ERR_UNSUPPORTED (-6) /* combination not provided (e.g. order 8 in 2D)           */
+
+/* Status-word bits (gks_status): which condition was seen by the device. */
+#define GKS_ST_RHO 1   /* a cell average with rho <= 0     */
+#define GKS_ST_P 2     /* a cell average with p <= 0       */
+#define GKS_ST_NAN 4   /* a non-finite cell average        */
+#define GKS_ST_FLUX 8  /* a face state the flux could not use (after the fallback) */
+
+typedef struct {
+    int dim;         /* 1, 2 or 3                                               */
+    int n[3];        /* cells per axis; unused axes must be 1                    */
+    double lo[3];    /* domain [lo, hi] per axis; the cell size h must be equal  */
+    double hi[3];    /*   on all active axes                                     */
+} gks_grid_t;
+
+typedef enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1 } gks_bc_t;
+
+typedef struct {
+    int precision;    /* 0: FP64 throughout; 1: reconstruction and flux in FP32,
+                         averages, gradients and stage combination in FP64       */
+    int limiter;      /* 0: GENO; 1: linear scheme (chi = 1)                     */
+    double C;         /* path-function steepness, Eq. HLP-weight (20)            */
+    double eps;       /* regulariser of the indicators, Eq. HLP-sp (1e-15)       */
+    double C0;        /* weight of the central 1D sub-stencil, Sec. 3.3 (8)      */
+    double c1_tau;    /* numerical collision time tau_n = c1 dt + c2 |pl - pr| /  */
+    double c2_tau;    /*   (pl + pr) dt in the relaxation factor (0.05, 1)        */
+    double adm_delta; /* a reconstructed face state whose rho or p is not above
+                         adm_delta times its cell's is replaced by the cell
+                         average with zero slopes (0.3)                          */
+    void *stream;     /* cudaStream_t for all work; NULL = legacy default stream */
+    void *workspace;  /* optional caller-owned device memory for all buffers     */
+    size_t workspace_bytes; /* its size; see gks_workspace_bytes                 */
+} gks_opts_t;
+
+typedef struct gks_ctx *gks_handle_t;
+
+/* Fill *o with the defaults above (precision 0, limiter 0, stream NULL,
+ * no workspace). */
+void gks_default_opts(gks_opts_t *o);
+
+/* Device bytes geno_gks_create needs for this grid and precision (state,
+ * stage buffers, reconstruction coefficients, face fluxes).  0 on a bad grid. */
+size_t gks_workspace_bytes(const gks_grid_t *grid, int precision);
+
+/* Number of faces F (all directions) of the grid; -1 on a bad grid. */
+long gks_face_count(const gks_grid_t *grid);
+
+/* Create a solver for the Euler equations with ratio of specific heats gamma
+ * (> 1) on `grid` with boundary condition `bc` on every side.
+ * order: 8 in 1D (Sec. 4.2), 4 in 2D/3D (Sec. 4.3); anything else gives
+ * GKS_ERR_UNSUPPORTED.  opts may be NULL (defaults).  If opts->workspace is
+ * given it must hold gks_workspace_bytes bytes (else GKS_ERR_OOM) and the
+ * library allocates no state memory of its own.  The state starts at zero;
+ * set it with gks_set_state.  *out receives the handle. */
+int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc, const gks_opts_t *opts,
+                    gks_handle_t *out);
+
+/* Copy the state in: W (nv x cells) and G (dim x nv x cells) doubles in the
+ * layouts above (host or device memory per on_device).  Clears the status
+ * word.  Synchronous with respect to the caller's buffers. */
+int gks_set_state(gks_handle_t h, const double *W, const double *G, int on_device);
+
+/* Copy the state out (same layouts).  Synchronises the stream; returns
+ * GKS_ERR_NONPHYSICAL (after copying) if the status word is set. */
+int gks_get_state(gks_handle_t h, double *W, double *G, int on_device);
+
+/* GENO interface states of the current state at every face Gauss point
+ * (Sec. 3, Eq. HLP; after the admissibility fallback described at
+ * adm_delta): face_states[side][v][c][g][face] doubles, side 0 = minus cell,
+ * c = 0 value, 1 + e = dW/dx_e (physical, global axes).  2 * nv * (dim + 1) *
+ * ng * F doubles.  Synchronises the stream. */
+int geno_reconstruct(gks_handle_t h, double *face_states, int on_device);
+
+/* Gas-kinetic interface quantities of the current state for a step dt > 0
+ * (Sec. 2): face_flux[q][v][g][face] doubles, q = 0 the flux F recovered at
+ * t^n from the time integrals over dt/2 and dt (F = (4 F(dt/2) - F(dt)) / dt),
+ * q = 1 its time derivative (4 (F(dt) - 2 F(dt/2)) / dt^2), q = 2 the
+ * interface state W(dt/2) used by the gradient update; the normal flux in
+ * global variable order.  3 * nv * ng * F doubles.  Synchronises the stream. */
+int gks_flux(gks_handle_t h, double dt, double *face_flux, int on_device);
+
+/* One two-stage fourth-order step of size dt > 0 (Sec. 2):
+ *   W*  = W^n + dt/2 L(F^n) + dt^2/8 L(dF^n/dt),  G* from W^n_face(dt/2);
+ *   W^{n+1} = W^n + dt L(F^n) + dt^2/6 (L(dF^n/dt) + 2 L((dF/dt)^s)),
+ *   G^{n+1} from W^s_face(dt/2)   (Eq. slope), superscript s = from (W*, G*),
+ * with L(F)_j = -(1/|Omega_j|) sum over the faces and Gauss points
+ * (Eq. semifvs).  Asynchronous. */
+int gks_step(gks_handle_t h, double dt);
+
+/* nsteps steps, each with dt = cfl h / max_cells max_d(|u_d| + c) computed on
+ * the device (no host round trip).  Asynchronous. */
+int gks_step_cfl(gks_handle_t h, double cfl, int nsteps);
+
+/* max over cells and axes of |u_d| + c of the current state.  Synchronises. */
+int gks_max_wavespeed(gks_handle_t h, double *out);
+
+/* Synchronise the stream and return the status word (>= 0, GKS_ST_* bits),
+ * or a negative GKS_ERR_* code if the device work itself failed. */
+int gks_status(gks_handle_t h);
+
+/* Free everything the handle owns (not a caller workspace).  NULL is a no-op. */
+int gks_destroy(gks_handle_t h);
+
+/* Message of the last error on this handle ("" if none); valid until the next
+ * call on the handle.  h == NULL gives the last create error of this thread. */
+const char *gks_last_error(gks_handle_t h);
+
+/* ------------------------------------------------------------------ */
+/* Batched mode: many independent 2D grids of uneven sizes              */
+/* ------------------------------------------------------------------ */
+typedef struct gks_batch_ctx *gks_batch_t;
+
+/* nbatch periodic-or-transmissive 2D grids, grid b with sides nx[b] x ny[b]
+ * cells and cell size hs[b].  Every grid keeps its own time step.
+ * precision as in gks_opts_t.  opts may be NULL. */
+int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs, double gamma, gks_bc_t bc,
+                     const gks_opts_t *opts, gks_batch_t *out);
+
+/* State of grid b (layouts as for a single 2D grid).  Host or device memory. */
+int gks_batch_set_state(gks_batch_t b, int grid, const double *W, const double *G, int on_device);
+int gks_batch_get_state(gks_batch_t b, int grid, double *W, double *G, int on_device);
+
+/* nsteps steps of every grid, grid b with dt_b = cfl h_b / (its max |u_d| + c)
+ * computed on the device.  The first call records one step into a CUDA graph
+ * (tile shapes from the built-in tuning table); later calls replay it.
+ * Asynchronous. */
+int gks_batch_run(gks_batch_t b, double cfl, int nsteps);
+
+/* Synchronise and return the status word (as gks_status). */
+int gks_batch_status(gks_batch_t b);
+
+int gks_batch_destroy(gks_batch_t b);
+const char *gks_batch_last_error(gks_batch_t b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

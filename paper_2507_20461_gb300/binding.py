@@ -1,0 +1,278 @@
+"""Thin ctypes binding of ``libgenogks.so`` (the C ABI in include/genogks.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Arrays may be torch CUDA tensors (device pointers, on the
+current torch stream) or numpy / CPU arrays (host pointers).  There is no
+CPU fallback: if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+ST_RHO, ST_P, ST_NAN, ST_FLUX = 1, 2, 4, 8
+BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+
+
+class GksError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"genogks error {code}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+class Opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int),
+        ("limiter", C.c_int),
+        ("C", C.c_double),
+        ("eps", C.c_double),
+        ("C0", C.c_double),
+        ("c1_tau", C.c_double),
+        ("c2_tau", C.c_double),
+        ("adm_delta", C.c_double),
+        ("stream", C.c_void_p),
+        ("workspace", C.c_void_p),
+        ("workspace_bytes", C.c_size_t),
+    ]
+
+
+_lib = None
+
+
+def lib(build: bool = True):
+    """Load (building first if needed) the in-tree library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgenogks.so not found at {path}; run __graft_entry__.build()")
+    L = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+    gp, op = C.POINTER(Grid), C.POINTER(Opts)
+    sig = {
+        "gks_default_opts": (None, [op]),
+        "gks_workspace_bytes": (C.c_size_t, [gp, C.c_int]),
+        "gks_face_count": (C.c_long, [gp]),
+        "geno_gks_create": (C.c_int, [gp, C.c_double, C.c_int, C.c_int, op, C.POINTER(vp)]),
+        "gks_set_state": (C.c_int, [vp, vp, vp, C.c_int]),
+        "gks_get_state": (C.c_int, [vp, vp, vp, C.c_int]),
+        "geno_reconstruct": (C.c_int, [vp, vp, C.c_int]),
+        "gks_flux": (C.c_int, [vp, C.c_double, vp, C.c_int]),
+        "gks_step": (C.c_int, [vp, C.c_double]),
+        "gks_step_cfl": (C.c_int, [vp, C.c_double, C.c_int]),
+        "gks_max_wavespeed": (C.c_int, [vp, dp]),
+        "gks_status": (C.c_int, [vp]),
+        "gks_destroy": (C.c_int, [vp]),
+        "gks_last_error": (C.c_char_p, [vp]),
+        "gks_batch_create": (C.c_int, [C.c_int, ip, ip, dp, C.c_double, C.c_int, op, C.POINTER(vp)]),
+        "gks_batch_set_state": (C.c_int, [vp, C.c_int, vp, vp, C.c_int]),
+        "gks_batch_get_state": (C.c_int, [vp, C.c_int, vp, vp, C.c_int]),
+        "gks_batch_run": (C.c_int, [vp, C.c_double, C.c_int]),
+        "gks_batch_status": (C.c_int, [vp]),
+        "gks_batch_destroy": (C.c_int, [vp]),
+        "gks_batch_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        if hasattr(L, name):
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """(pointer, on_device) of a torch tensor or numpy array of float64."""
+    try:
+        import torch
+
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise ValueError("tensors must be contiguous float64")
+            return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    except ImportError:
+        pass
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise ValueError("arrays must be C-contiguous float64")
+    return C.c_void_p(a.ctypes.data), 0
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    return C.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    lib().gks_default_opts(C.byref(o))
+    return o
+
+
+def make_grid(n, lo=None, hi=None) -> Grid:
+    dim = len(n)
+    nn = list(n) + [1] * (3 - dim)
+    lo = list(lo) if lo is not None else [0.0] * dim
+    hi = list(hi) if hi is not None else [1.0] * dim
+    lo += [0.0] * (3 - dim)
+    hi += [1.0] * (3 - dim)
+    return Grid(dim, (C.c_int * 3)(*nn), (C.c_double * 3)(*lo), (C.c_double * 3)(*hi))
+
+
+def _check(h, r, fn="gks_last_error"):
+    if r < 0:
+        msg = getattr(lib(), fn)(h)
+        raise GksError(r, msg.decode() if msg else "")
+    return r
+
+
+def face_count(grid: Grid) -> int:
+    return int(lib().gks_face_count(C.byref(grid)))
+
+
+def workspace_bytes(grid: Grid, precision: int = 0) -> int:
+    return int(lib().gks_workspace_bytes(C.byref(grid), precision))
+
+
+def geno_gks_create(grid: Grid, gamma: float, order: int, bc: int, opts: Opts | None = None):
+    h = C.c_void_p()
+    r = lib().geno_gks_create(C.byref(grid), gamma, order, bc, C.byref(opts) if opts is not None else None, C.byref(h))
+    _check(None, r)
+    return h
+
+
+def gks_set_state(h, W, G):
+    pw, dw = _ptr(W)
+    pg, dg = _ptr(G)
+    if dw != dg:
+        raise ValueError("W and G must both be on the device or both on the host")
+    return _check(h, lib().gks_set_state(h, pw, pg, dw))
+
+
+def gks_get_state(h, W, G):
+    pw, dw = _ptr(W)
+    pg, dg = _ptr(G)
+    if dw != dg:
+        raise ValueError("W and G must both be on the device or both on the host")
+    return _check(h, lib().gks_get_state(h, pw, pg, dw))
+
+
+def geno_reconstruct(h, out):
+    p, d = _ptr(out)
+    return _check(h, lib().geno_reconstruct(h, p, d))
+
+
+def gks_flux(h, dt: float, out):
+    p, d = _ptr(out)
+    return _check(h, lib().gks_flux(h, float(dt), p, d))
+
+
+def gks_step(h, dt: float):
+    return _check(h, lib().gks_step(h, float(dt)))
+
+
+def gks_step_cfl(h, cfl: float, nsteps: int):
+    return _check(h, lib().gks_step_cfl(h, float(cfl), int(nsteps)))
+
+
+def gks_max_wavespeed(h) -> float:
+    s = C.c_double()
+    _check(h, lib().gks_max_wavespeed(h, C.byref(s)))
+    return s.value
+
+
+def gks_status(h) -> int:
+    return _check(h, lib().gks_status(h))
+
+
+def gks_destroy(h):
+    return lib().gks_destroy(h)
+
+
+def gks_last_error(h) -> str:
+    m = lib().gks_last_error(h)
+    return m.decode() if m else ""
+
+
+class Solver:
+    """Handle wrapper: ``Solver(n=(nx, ny), lo, hi, gamma, bc, precision)``."""
+
+    def __init__(self, n, lo=None, hi=None, gamma=1.4, bc=BC_PERIODIC, precision=0, limiter=0, stream=None, **consts):
+        self.grid = make_grid(n, lo, hi)
+        self.dim = len(n)
+        self.nv = self.dim + 2
+        self.n = tuple(n)
+        o = default_opts()
+        o.precision = precision
+        o.limiter = limiter
+        for k, v in consts.items():
+            setattr(o, k, v)
+        sp = _stream_ptr(stream)
+        o.stream = sp.value if sp is not None else None
+        self.opts = o
+        self.h = geno_gks_create(self.grid, gamma, 8 if self.dim == 1 else 4, bc, o)
+
+    @property
+    def shape(self):
+        return tuple(reversed(self.n))
+
+    @property
+    def nfaces(self):
+        return face_count(self.grid)
+
+    @property
+    def ngauss(self):
+        return {1: 1, 2: 2, 3: 4}[self.dim]
+
+    def set_state(self, W, G):
+        gks_set_state(self.h, W, G)
+
+    def get_state(self, W, G):
+        gks_get_state(self.h, W, G)
+
+    def reconstruct(self, out):
+        geno_reconstruct(self.h, out)
+
+    def flux(self, dt, out):
+        gks_flux(self.h, dt, out)
+
+    def step(self, dt):
+        gks_step(self.h, dt)
+
+    def step_cfl(self, cfl, nsteps=1):
+        gks_step_cfl(self.h, cfl, nsteps)
+
+    def max_wavespeed(self):
+        return gks_max_wavespeed(self.h)
+
+    def status(self):
+        return gks_status(self.h)
+
+    def close(self):
+        if self.h is not None:
+            gks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,445 @@
+/* C ABI of libgenogks: handle lifetime, state transfer, and the step driver.
+ * The numerics are in kernels.cuh / gks_device.cuh; see include/genogks.h
+ * for the contract of every entry point. */
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace {
+
+thread_local char g_create_err[256] = "";
+
+int fail(gks_ctx *c, int code, const char *fmt, ...)
+{
+    char *buf = c ? c->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(gks_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, GKS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t W, G, Ws, Gs, Acc, small, B, ff, total;
+    size_t B_elems, ff_elems;
+};
+
+bool grid_ok(const gks_grid_t *g, double *h)
+{
+    if (!g || g->dim < 1 || g->dim > 3) return false;
+    double hh = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (a < g->dim) {
+            if (g->n[a] < 1 || g->n[a] > (1 << 24)) return false;
+            const double ha = (g->hi[a] - g->lo[a]) / g->n[a];
+            if (!(ha > 0.0) || !std::isfinite(ha)) return false;
+            if (a == 0) hh = ha;
+            else if (std::fabs(ha - hh) > 1e-12 * hh) return false;
+        } else if (g->n[a] != 1) {
+            return false;
+        }
+    }
+    if (h) *h = hh;
+    return true;
+}
+
+long face_count(const gks_grid_t *g)
+{
+    long r = 0;
+    for (int d = 0; d < g->dim; ++d) {
+        long f = 1;
+        for (int a = 0; a < g->dim; ++a) f *= (a == d) ? (g->n[a] + 1) : g->n[a];
+        r += f;
+    }
+    return r;
+}
+
+Layout layout(const gks_grid_t *g, int precision)
+{
+    Layout L{};
+    const int m = g->dim, nv = m + 2, ng = gks::ngauss(m);
+    long ncell = 1, next = 1;
+    for (int a = 0; a < m; ++a) {
+        ncell *= g->n[a];
+        next *= g->n[a] + 2;
+    }
+    const size_t rs = precision ? sizeof(float) : sizeof(double);
+    L.B_elems = (m >= 2) ? (size_t)nv * gks::ncubic(m) * next : 0;
+    L.ff_elems = (size_t)3 * nv * ng * face_count(g);
+    size_t off = 0;
+    L.W = off; off = align_up(off + sizeof(double) * nv * ncell);
+    L.G = off; off = align_up(off + sizeof(double) * m * nv * ncell);
+    L.Ws = off; off = align_up(off + sizeof(double) * nv * ncell);
+    L.Gs = off; off = align_up(off + sizeof(double) * m * nv * ncell);
+    L.Acc = off; off = align_up(off + sizeof(double) * nv * ncell);
+    L.small = off; off = align_up(off + 256);
+    L.B = off; off = align_up(off + rs * L.B_elems);
+    L.ff = off; off = align_up(off + rs * L.ff_elems);
+    L.total = off;
+    return L;
+}
+
+int sync_status(gks_ctx *c)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    int st = 0;
+    e = cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    return st;
+}
+
+int stage_buffer(gks_ctx *c, size_t bytes)
+{
+    if (c->stage_bytes >= bytes) return GKS_OK;
+    if (c->stage_out) cudaFree(c->stage_out);
+    c->stage_out = nullptr;
+    c->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->stage_out, bytes);
+    if (e != cudaSuccess) return fail(c, GKS_ERR_OOM, "staging buffer of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    c->stage_bytes = bytes;
+    return GKS_OK;
+}
+
+__global__ void widen_kernel(const float *__restrict__ in, double *__restrict__ out, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+cudaError_t run_flux(gks_ctx *c, const double *W, const double *G)
+{
+    switch (c->dim) {
+    case 1: return gks::launch_flux<1>(c, W, G);
+    case 2: return gks::launch_flux<2>(c, W, G);
+    default: return gks::launch_flux<3>(c, W, G);
+    }
+}
+
+cudaError_t run_update(gks_ctx *c, int stage)
+{
+    switch (c->dim) {
+    case 1: return gks::launch_update<1>(c, stage);
+    case 2: return gks::launch_update<2>(c, stage);
+    default: return gks::launch_update<3>(c, stage);
+    }
+}
+
+cudaError_t run_wavespeed(gks_ctx *c, double cfl)
+{
+    switch (c->dim) {
+    case 1: return gks::launch_wavespeed<1>(c, cfl);
+    case 2: return gks::launch_wavespeed<2>(c, cfl);
+    default: return gks::launch_wavespeed<3>(c, cfl);
+    }
+}
+
+/* both stages with the time step already in c->dt */
+int two_stages(gks_ctx *c)
+{
+    cudaError_t e;
+    if ((e = run_flux(c, c->W, c->G)) != cudaSuccess) return cuda_fail(c, e, "stage 1 flux");
+    if ((e = run_update(c, 1)) != cudaSuccess) return cuda_fail(c, e, "stage 1 update");
+    if ((e = run_flux(c, c->Ws, c->Gs)) != cudaSuccess) return cuda_fail(c, e, "stage 2 flux");
+    if ((e = run_update(c, 2)) != cudaSuccess) return cuda_fail(c, e, "stage 2 update");
+    return GKS_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+void gks_default_opts(gks_opts_t *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = 0;
+    o->limiter = 0;
+    o->C = 20.0;
+    o->eps = 1e-15;
+    o->C0 = 8.0;
+    o->c1_tau = 0.05;
+    o->c2_tau = 1.0;
+    o->adm_delta = 0.3;
+}
+
+size_t gks_workspace_bytes(const gks_grid_t *grid, int precision)
+{
+    if (!grid_ok(grid, nullptr) || (precision != 0 && precision != 1)) return 0;
+    return layout(grid, precision).total;
+}
+
+long gks_face_count(const gks_grid_t *grid)
+{
+    if (!grid_ok(grid, nullptr)) return -1;
+    return face_count(grid);
+}
+
+int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc, const gks_opts_t *opts,
+                    gks_handle_t *out)
+{
+    if (!out) return fail(nullptr, GKS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    double h = 0.0;
+    if (!grid_ok(grid, &h)) return fail(nullptr, GKS_ERR_ARG, "invalid grid (dim 1..3, n >= 1, equal cell size)");
+    if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(nullptr, GKS_ERR_ARG, "gamma must be > 1");
+    if (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE) return fail(nullptr, GKS_ERR_ARG, "unknown boundary condition");
+    const int want = (grid->dim == 1) ? 8 : 4;
+    if (order != want)
+        return fail(nullptr, GKS_ERR_UNSUPPORTED, "order %d is not provided in %dD (use %d)", order, grid->dim, want);
+    gks_opts_t o;
+    gks_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != 0 && o.precision != 1) return fail(nullptr, GKS_ERR_ARG, "precision must be 0 or 1");
+    if (o.limiter != 0 && o.limiter != 1) return fail(nullptr, GKS_ERR_ARG, "limiter must be 0 or 1");
+    if (!(o.C > 0.0) || !(o.eps > 0.0) || !(o.C0 > 0.0) || !(o.c1_tau >= 0.0) || !(o.c2_tau >= 0.0) ||
+        !(o.adm_delta >= 0.0) || !(o.adm_delta < 1.0))
+        return fail(nullptr, GKS_ERR_ARG, "invalid scheme constants");
+
+    gks_ctx *c = new (std::nothrow) gks_ctx;
+    if (!c) return fail(nullptr, GKS_ERR_OOM, "host allocation");
+    std::memset(c, 0, sizeof(*c));
+    c->dim = grid->dim;
+    c->nv = grid->dim + 2;
+    c->ng = gks::ngauss(grid->dim);
+    c->precision = o.precision;
+    c->order = order;
+    for (int a = 0; a < 3; ++a) c->n[a] = grid->n[a];
+    c->h = h;
+    c->gamma = gamma;
+    c->opts = o;
+    c->stream = (cudaStream_t)o.stream;
+
+    const Layout L = layout(grid, o.precision);
+    if (o.workspace) {
+        if (o.workspace_bytes < L.total || ((size_t)o.workspace & 255)) {
+            delete c;
+            return fail(nullptr, GKS_ERR_OOM, "workspace needs %zu bytes, 256-byte aligned", L.total);
+        }
+        c->ws = o.workspace;
+        c->own_ws = 0;
+    } else {
+        cudaError_t e = cudaMalloc(&c->ws, L.total);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(nullptr, GKS_ERR_OOM, "cudaMalloc of %zu bytes: %s", L.total, cudaGetErrorString(e));
+        }
+        c->own_ws = 1;
+    }
+    c->ws_bytes = L.total;
+    char *base = (char *)c->ws;
+    c->W = (double *)(base + L.W);
+    c->G = (double *)(base + L.G);
+    c->Ws = (double *)(base + L.Ws);
+    c->Gs = (double *)(base + L.Gs);
+    c->Acc = (double *)(base + L.Acc);
+    c->dt = (double *)(base + L.small);
+    c->smax = (unsigned long long *)(base + L.small + 64);
+    c->status = (int *)(base + L.small + 128);
+    c->B = base + L.B;
+    c->ff = base + L.ff;
+    c->B_elems = L.B_elems;
+    c->ff_elems = L.ff_elems;
+
+    gks::KP &P = c->kp;
+    std::memset(&P, 0, sizeof(P));
+    long ncell = 1, next = 1;
+    for (int a = 0; a < 3; ++a) {
+        P.n[a] = grid->n[a];
+        P.ext[a] = (a < grid->dim) ? grid->n[a] + 2 : 1;
+        ncell *= grid->n[a];
+        next *= P.ext[a];
+    }
+    P.ncell = ncell;
+    P.next = next;
+    long off = 0;
+    for (int d = 0; d < grid->dim; ++d) {
+        long f = 1;
+        for (int a = 0; a < grid->dim; ++a) f *= (a == d) ? (grid->n[a] + 1) : grid->n[a];
+        P.nface[d] = f;
+        P.foff[d] = off;
+        off += f;
+    }
+    P.nftot = off;
+    P.bc = (int)bc;
+    P.limiter = o.limiter;
+    P.h = h;
+    P.ih = 1.0 / h;
+    P.gamma = gamma;
+    P.C = o.C;
+    P.itanhC = 1.0 / std::tanh(o.C);
+    P.eps = o.eps;
+    P.C0 = o.C0;
+    P.adm = o.adm_delta;
+    P.fp.gamma = gamma;
+    P.fp.c1 = o.c1_tau;
+    P.fp.c2 = o.c2_tau;
+
+    cudaError_t e = cudaMemsetAsync(c->ws, 0, L.total, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        int r = cuda_fail(nullptr, e, "workspace clear");
+        if (c->own_ws) cudaFree(c->ws);
+        delete c;
+        return r;
+    }
+    *out = c;
+    return GKS_OK;
+}
+
+int gks_set_state(gks_handle_t c, const double *W, const double *G, int on_device)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    if (!W || !G) return fail(c, GKS_ERR_ARG, "W and G are required");
+    const size_t nW = (size_t)c->nv * c->kp.ncell, nG = (size_t)c->dim * nW;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(c->W, W, nW * sizeof(double), k, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->G, G, nG * sizeof(double), k, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+    c->err[0] = 0;
+    return GKS_OK;
+}
+
+int gks_get_state(gks_handle_t c, double *W, double *G, int on_device)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    const size_t nW = (size_t)c->nv * c->kp.ncell, nG = (size_t)c->dim * nW;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    if (W) e = cudaMemcpyAsync(W, c->W, nW * sizeof(double), k, c->stream);
+    if (e == cudaSuccess && G) e = cudaMemcpyAsync(G, c->G, nG * sizeof(double), k, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
+    const int st = sync_status(c);
+    if (st < 0) return st;
+    if (st) return fail(c, GKS_ERR_NONPHYSICAL, "non-physical state (status bits 0x%x)", st);
+    return GKS_OK;
+}
+
+int geno_reconstruct(gks_handle_t c, double *fs, int on_device)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    if (!fs) return fail(c, GKS_ERR_ARG, "face_states is NULL");
+    const size_t n = (size_t)2 * c->nv * (c->dim + 1) * c->ng * c->kp.nftot;
+    double *dst = fs;
+    if (!on_device) {
+        int r = stage_buffer(c, n * sizeof(double));
+        if (r) return r;
+        dst = c->stage_out;
+    }
+    cudaError_t e;
+    switch (c->dim) {
+    case 1: e = gks::launch_states<1>(c, c->W, c->G, dst); break;
+    case 2: e = gks::launch_states<2>(c, c->W, c->G, dst); break;
+    default: e = gks::launch_states<3>(c, c->W, c->G, dst); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "reconstruct");
+    if (!on_device) {
+        e = cudaMemcpyAsync(fs, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "reconstruct copy");
+    }
+    const int st = sync_status(c);
+    return st < 0 ? st : GKS_OK;
+}
+
+int gks_flux(gks_handle_t c, double dt, double *out, int on_device)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    if (!out) return fail(c, GKS_ERR_ARG, "face_flux is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GKS_ERR_ARG, "dt must be finite and > 0");
+    gks::set_scalar_kernel<<<1, 1, 0, c->stream>>>(c->dt, dt);
+    cudaError_t e = run_flux(c, c->W, c->G);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flux");
+    const size_t n = c->ff_elems;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (c->precision == 0) {
+        e = cudaMemcpyAsync(out, c->ff, n * sizeof(double), k, c->stream);
+    } else {
+        double *dst = out;
+        if (!on_device) {
+            int r = stage_buffer(c, n * sizeof(double));
+            if (r) return r;
+            dst = c->stage_out;
+        }
+        widen_kernel<<<gks::blocks_for((long)n, 256) > 4096 ? 4096 : gks::blocks_for((long)n, 256), 256, 0,
+                       c->stream>>>((const float *)c->ff, dst, n);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(out, dst, n * sizeof(double), k, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "flux copy");
+    const int st = sync_status(c);
+    if (st < 0) return st;
+    if (st & GKS_ST_FLUX) return fail(c, GKS_ERR_NONPHYSICAL, "a face state was not admissible (status 0x%x)", st);
+    return GKS_OK;
+}
+
+int gks_step(gks_handle_t c, double dt)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GKS_ERR_ARG, "dt must be finite and > 0");
+    gks::set_scalar_kernel<<<1, 1, 0, c->stream>>>(c->dt, dt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "set dt");
+    return two_stages(c);
+}
+
+int gks_step_cfl(gks_handle_t c, double cfl, int nsteps)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    if (!(cfl > 0.0) || !std::isfinite(cfl) || nsteps < 0) return fail(c, GKS_ERR_ARG, "cfl > 0 and nsteps >= 0 required");
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e = run_wavespeed(c, cfl);
+        if (e != cudaSuccess) return cuda_fail(c, e, "time step");
+        int r = two_stages(c);
+        if (r) return r;
+    }
+    return GKS_OK;
+}
+
+int gks_max_wavespeed(gks_handle_t c, double *out)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    if (!out) return fail(c, GKS_ERR_ARG, "out is NULL");
+    cudaError_t e = run_wavespeed(c, 0.0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "wavespeed");
+    unsigned long long bits = 0;
+    e = cudaMemcpyAsync(&bits, c->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "wavespeed read");
+    double s;
+    std::memcpy(&s, &bits, sizeof(s));
+    *out = s;
+    if (!std::isfinite(s) || s >= 1e299) return fail(c, GKS_ERR_NONPHYSICAL, "non-finite wave speed");
+    return GKS_OK;
+}
+
+int gks_status(gks_handle_t c)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    return sync_status(c);
+}
+
+int gks_destroy(gks_handle_t c)
+{
+    if (!c) return GKS_OK;
+    cudaStreamSynchronize(c->stream);
+    if (c->stage_out) cudaFree(c->stage_out);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    delete c;
+    return GKS_OK;
+}
+
+const char *gks_last_error(gks_handle_t c) { return c ? c->err : g_create_err; }
+
+} // extern "C"

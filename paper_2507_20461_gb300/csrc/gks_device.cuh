@@ -1,0 +1,343 @@
+/*
+ * Gas-kinetic interface flux for the Euler equations (device code).
+ *
+ * The paper (Sec. 2) takes the flux from the time-dependent gas distribution
+ * function of the GKS and defers its formulas to earlier work; this is the
+ * BGK solution at an interface Gauss point in the face frame (velocity
+ * component 0 and derivative axis 0 along the face normal):
+ *
+ *   f(0,t) = (1-e) g0 + t e (T0 g0) + t (A0 g0)
+ *          + e [ (1 - t T_l) H(u) g_l + (1 - t T_r) H(-u) g_r ],   e = exp(-t/tau_n),
+ *
+ * with T = sum_e a_e u_e the spatial micro-slopes (left, right, and the
+ * equilibrium one from the mean of the left/right derivatives), A0 the
+ * equilibrium time slope from the compatibility condition, the physical
+ * collision time 0 (Euler) in the Chapman-Enskog terms and the numerical one
+ * tau_n = C1 dt + C2 |pl - pr| / (pl + pr) dt in the relaxation factor.
+ *
+ * Closed forms used here (all exact rearrangements of the velocity
+ * integrals):
+ *   rho0 <u psi>_0        = Euler flux of W0;
+ *   rho0 <T0 psi>_0       = sum_e dF_e/dx_e(W0) = -dW0/dt;
+ *   rho0 <A0 u psi>_0     = dF_n/dt = F_n'(W0) dW0/dt;
+ *   time integrals over [0, d]: int (1-e) = d - ie, int t e = ite,
+ *     ie = tau_n (1 - e_d), ite = tau_n^2 - tau_n (d + tau_n) e_d.
+ * With the integrated fluxes over dt/2 and dt, F = (4 F(dt/2) - F(dt)) / dt
+ * and dF/dt = 4 (F(dt) - 2 F(dt/2)) / dt^2 reduce to
+ *   F  = F0 + (4 ie_h - ie_1)/dt (Fk - F0) + (4 ite_h - ite_1)/dt (FT0 - FTk),
+ *   Ft = FA0 + 4 (ie_1 - 2 ie_h)/dt^2 (Fk - F0) + 4 (ite_1 - 2 ite_h)/dt^2 (FT0 - FTk),
+ * and the interface state W(dt/2) = W0 + t (1 - e_t) dW0/dt - t e_t WTk.
+ */
+#pragma once
+#include <cuda_runtime.h>
+
+namespace gks {
+
+template <typename R> struct RT;
+template <> struct RT<double> {
+    __device__ static double erfc_(double x) { return erfc(x); }
+    __device__ static double exp_(double x) { return exp(x); }
+    __device__ static double sqrt_(double x) { return sqrt(x); }
+    __device__ static double rsqrt_(double x) { return rsqrt(x); }
+    __device__ static double tanh_(double x) { return tanh(x); }
+    __device__ static double abs_(double x) { return fabs(x); }
+};
+template <> struct RT<float> {
+    __device__ static float erfc_(float x) { return erfcf(x); }
+    __device__ static float exp_(float x) { return expf(x); }
+    __device__ static float sqrt_(float x) { return sqrtf(x); }
+    __device__ static float rsqrt_(float x) { return rsqrtf(x); }
+    __device__ static float tanh_(float x) { return tanhf(x); }
+    __device__ static float abs_(float x) { return fabsf(x); }
+};
+
+/* Primitive description of a Maxwellian: density, velocity, 1/(2 lambda) = p/rho. */
+template <typename R, int M> struct Prim {
+    R rho, U[3], p, i2l; /* i2l = 1 / (2 lambda) */
+};
+
+template <typename R, int M>
+__device__ __forceinline__ bool to_prim(const R *W, R gm1, Prim<R, M> &P)
+{
+    P.rho = W[0];
+    const R inv = R(1) / W[0];
+    R ke = R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) P.U[a] = R(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        P.U[a] = W[1 + a] * inv;
+        ke += P.U[a] * W[1 + a];
+    }
+    P.p = gm1 * (W[M + 1] - R(0.5) * ke);
+    P.i2l = P.p * inv;
+    return (W[0] > R(0)) && (P.p > R(0));
+}
+
+/* Moments of a Maxwellian: u-moments (full or half space), full v, w moments,
+ * and <xi^2>, <xi^4> of the K internal degrees of freedom. */
+template <typename R, int M> struct Mom {
+    R u[7];
+    R v[6];
+    R w[6];
+    R xi[3];
+};
+
+template <typename R, int N>
+__device__ __forceinline__ void full_moments(R U, R i2l, R *m)
+{
+    m[0] = R(1);
+    m[1] = U;
+#pragma unroll
+    for (int k = 0; k + 2 < N; ++k) m[k + 2] = U * m[k + 1] + R(k + 1) * i2l * m[k];
+}
+
+/* half-space u moments: sign = +1 integrates u > 0, -1 integrates u < 0 */
+template <typename R, int N>
+__device__ __forceinline__ void half_moments(R U, R rho, R p, R i2l, int sign, R *m)
+{
+    const R sl = RT<R>::sqrt_(R(0.5) * rho / p); /* sqrt(lambda) */
+    const R x = sl * U;
+    const R s = R(sign);
+    m[0] = R(0.5) * RT<R>::erfc_(-s * x);
+    /* exp(-lambda U^2) / (2 sqrt(pi lambda)) */
+    m[1] = U * m[0] + s * R(0.5) * RT<R>::exp_(-x * x) * R(0.56418958354775628) / sl;
+#pragma unroll
+    for (int k = 0; k + 2 < N; ++k) m[k + 2] = U * m[k + 1] + R(k + 1) * i2l * m[k];
+}
+
+template <typename R, int M>
+__device__ __forceinline__ void tangential_and_internal(const Prim<R, M> &P, R K, Mom<R, M> &T)
+{
+    if constexpr (M >= 2) full_moments<R, 6>(P.U[1], P.i2l, T.v);
+    if constexpr (M >= 3) full_moments<R, 6>(P.U[2], P.i2l, T.w);
+    T.xi[0] = R(1);
+    T.xi[1] = K * P.i2l;
+    T.xi[2] = K * (K + R(2)) * P.i2l * P.i2l;
+}
+
+/* <u^a v^b w^c xi^(2d)> */
+template <typename R, int M, int A, int B, int C, int D>
+__device__ __forceinline__ R mono(const Mom<R, M> &T)
+{
+    static_assert(A <= 6 && B <= 5 && C <= 5 && D <= 2, "moment order");
+    R r = T.u[A];
+    if constexpr (M >= 2 && B > 0) r *= T.v[B];
+    if constexpr (M >= 3 && C > 0) r *= T.w[C];
+    if constexpr (D > 0) r *= T.xi[D];
+    return r;
+}
+
+/* <s u^A v^B w^C xi^(2D)> for s = s0 + s1 u (+ s2 v + s3 w) + sE (|u|^2 + xi^2)/2 */
+template <typename R, int M, int A, int B, int C, int D>
+__device__ __forceinline__ R mom_s(const Mom<R, M> &T, const R *s)
+{
+    R r = s[0] * mono<R, M, A, B, C, D>(T) + s[1] * mono<R, M, A + 1, B, C, D>(T);
+    R e = mono<R, M, A + 2, B, C, D>(T) + mono<R, M, A, B, C, D + 1>(T);
+    if constexpr (M >= 2) {
+        r += s[2] * mono<R, M, A, B + 1, C, D>(T);
+        e += mono<R, M, A, B + 2, C, D>(T);
+    }
+    if constexpr (M >= 3) {
+        r += s[3] * mono<R, M, A, B, C + 1, D>(T);
+        e += mono<R, M, A, B, C + 2, D>(T);
+    }
+    return r + R(0.5) * s[M + 1] * e;
+}
+
+/* out[b] += <psi_b u^A v^B w^C s> for every b */
+template <typename R, int M, int A, int B, int C>
+__device__ __forceinline__ void psi_mom_s(const Mom<R, M> &T, const R *s, R *out)
+{
+    out[0] += mom_s<R, M, A, B, C, 0>(T, s);
+    out[1] += mom_s<R, M, A + 1, B, C, 0>(T, s);
+    if constexpr (M >= 2) out[2] += mom_s<R, M, A, B + 1, C, 0>(T, s);
+    if constexpr (M >= 3) out[3] += mom_s<R, M, A, B, C + 1, 0>(T, s);
+    R e = mom_s<R, M, A + 2, B, C, 0>(T, s) + mom_s<R, M, A, B, C, 1>(T, s);
+    if constexpr (M >= 2) e += mom_s<R, M, A, B + 2, C, 0>(T, s);
+    if constexpr (M >= 3) e += mom_s<R, M, A, B, C + 2, 0>(T, s);
+    out[M + 1] += R(0.5) * e;
+}
+
+/* out[b] = <psi_b u^K T>, T = sum_e s_e u_e (slopes along the face axes) */
+template <typename R, int M, int K>
+__device__ __forceinline__ void psi_mom_T(const Mom<R, M> &T, const R (*s)[M + 2], R *out)
+{
+#pragma unroll
+    for (int b = 0; b < M + 2; ++b) out[b] = R(0);
+    psi_mom_s<R, M, K + 1, 0, 0>(T, s[0], out);
+    if constexpr (M >= 2) psi_mom_s<R, M, K, 1, 0>(T, s[1], out);
+    if constexpr (M >= 3) psi_mom_s<R, M, K, 0, 1>(T, s[2], out);
+}
+
+/* Micro-slope a (coefficients on 1, u, v, w, (|u|^2+xi^2)/2) with <a psi> = r,
+ * closed form through the peculiar velocity c = u - U:
+ * <c_i a> = alpha_i / (2 lambda), and the two scalar moments give alpha_1, alpha_E. */
+template <typename R, int M>
+__device__ __forceinline__ void slope(const Prim<R, M> &P, R Ntot, const R *r, R *a)
+{
+    R sv[3], Us = R(0), U2 = R(0);
+    const R s0 = r[0];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        sv[i] = r[1 + i] - P.U[i] * s0;
+        Us += P.U[i] * sv[i];
+        U2 += P.U[i] * P.U[i];
+    }
+    const R sE = r[M + 1] - R(0.5) * U2 * s0 - Us;
+    const R lam = R(0.5) / P.i2l;
+    const R aE = R(8) * lam * lam / Ntot * sE - R(2) * lam * s0;
+    const R a1 = s0 - aE * Ntot * R(0.5) * P.i2l;
+    R aU = R(0);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const R al = R(2) * lam * sv[i];
+        aU += al * P.U[i];
+        a[1 + i] = al - aE * P.U[i];
+    }
+    a[0] = a1 - aU + R(0.5) * aE * U2;
+    a[M + 1] = aE;
+}
+
+/* Euler flux along face axis e of the state (P, W) */
+template <typename R, int M>
+__device__ __forceinline__ void euler_flux(const Prim<R, M> &P, const R *W, int e, R *F)
+{
+    const R ue = P.U[e];
+    F[0] = W[1 + e];
+#pragma unroll
+    for (int i = 0; i < M; ++i) F[1 + i] = W[1 + i] * ue + (i == e ? P.p : R(0));
+    F[M + 1] = ue * (W[M + 1] + P.p);
+}
+
+/* dF_e for a variation dW of the conservative variables (Jacobian-vector product) */
+template <typename R, int M>
+__device__ __forceinline__ void euler_dflux(const Prim<R, M> &P, const R *W, R gm1, int e, const R *dW, R *dF)
+{
+    const R inv = R(1) / P.rho;
+    R dU[3], UdU = R(0), U2 = R(0);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        dU[i] = (dW[1 + i] - P.U[i] * dW[0]) * inv;
+        UdU += P.U[i] * dU[i];
+        U2 += P.U[i] * P.U[i];
+    }
+    const R dp = gm1 * (dW[M + 1] - R(0.5) * U2 * dW[0] - P.rho * UdU);
+    dF[0] = dW[1 + e];
+#pragma unroll
+    for (int i = 0; i < M; ++i) dF[1 + i] = dW[1 + i] * P.U[e] + W[1 + i] * dU[e] + (i == e ? dp : R(0));
+    dF[M + 1] = dU[e] * (W[M + 1] + P.p) + P.U[e] * (dW[M + 1] + dp);
+}
+
+struct FluxParams {
+    double gamma, c1, c2;
+};
+
+/* Returns false (and leaves outputs untouched) when a state is not admissible. */
+template <typename R, int M>
+__device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *Wl, const R *Wr, const R (*dWl)[M + 2],
+                                          const R (*dWr)[M + 2], R *F, R *Ft, R *Wh)
+{
+    constexpr int NV = M + 2;
+    const R gm1 = R(fp.gamma - 1.0);
+    const R Ntot = R(2.0 / (fp.gamma - 1.0));
+    const R K = Ntot - R(M);
+    Prim<R, M> Pl, Pr, P0;
+    if (!to_prim<R, M>(Wl, gm1, Pl) || !to_prim<R, M>(Wr, gm1, Pr)) return false;
+
+    Mom<R, M> Tl, Tr, T0;
+    half_moments<R, 7>(Pl.U[0], Pl.rho, Pl.p, Pl.i2l, +1, Tl.u);
+    half_moments<R, 7>(Pr.U[0], Pr.rho, Pr.p, Pr.i2l, -1, Tr.u);
+    tangential_and_internal<R, M>(Pl, K, Tl);
+    tangential_and_internal<R, M>(Pr, K, Tr);
+
+    /* equilibrium state: kinetic collision of the two half streams */
+    R W0[NV], Fk[NV];
+    {
+        R el = Tl.xi[1], er = Tr.xi[1];
+        if constexpr (M >= 2) { el += Tl.v[2]; er += Tr.v[2]; }
+        if constexpr (M >= 3) { el += Tl.w[2]; er += Tr.w[2]; }
+        W0[0] = Pl.rho * Tl.u[0] + Pr.rho * Tr.u[0];
+        W0[1] = Pl.rho * Tl.u[1] + Pr.rho * Tr.u[1];
+        Fk[0] = W0[1];
+        Fk[1] = Pl.rho * Tl.u[2] + Pr.rho * Tr.u[2];
+#pragma unroll
+        for (int i = 1; i < M; ++i) {
+            W0[1 + i] = Pl.rho * Tl.u[0] * Pl.U[i] + Pr.rho * Tr.u[0] * Pr.U[i];
+            Fk[1 + i] = Pl.rho * Tl.u[1] * Pl.U[i] + Pr.rho * Tr.u[1] * Pr.U[i];
+        }
+        W0[M + 1] = R(0.5) * (Pl.rho * (Tl.u[2] + Tl.u[0] * el) + Pr.rho * (Tr.u[2] + Tr.u[0] * er));
+        Fk[M + 1] = R(0.5) * (Pl.rho * (Tl.u[3] + Tl.u[1] * el) + Pr.rho * (Tr.u[3] + Tr.u[1] * er));
+    }
+    if (!to_prim<R, M>(W0, gm1, P0)) return false;
+    full_moments<R, 7>(P0.U[0], P0.i2l, T0.u);
+    tangential_and_internal<R, M>(P0, K, T0);
+
+    /* micro-slopes along every face axis */
+    R sl[M][NV], sr[M][NV], s0[M][NV], dW0[M][NV];
+    {
+        const R il = R(1) / Pl.rho, ir = R(1) / Pr.rho, i0 = R(1) / P0.rho;
+#pragma unroll
+        for (int e = 0; e < M; ++e) {
+            R rl[NV], rr[NV], r0[NV];
+#pragma unroll
+            for (int b = 0; b < NV; ++b) {
+                rl[b] = dWl[e][b] * il;
+                rr[b] = dWr[e][b] * ir;
+                dW0[e][b] = R(0.5) * (dWl[e][b] + dWr[e][b]);
+                r0[b] = dW0[e][b] * i0;
+            }
+            slope<R, M>(Pl, Ntot, rl, sl[e]);
+            slope<R, M>(Pr, Ntot, rr, sr[e]);
+            slope<R, M>(P0, Ntot, r0, s0[e]);
+        }
+    }
+    /* dW0/dt = -sum_e dF_e/dx_e, dF_n/dt, Euler flux of W0 */
+    R W0t[NV], FA0[NV], F0[NV];
+    {
+#pragma unroll
+        for (int b = 0; b < NV; ++b) W0t[b] = R(0);
+#pragma unroll
+        for (int e = 0; e < M; ++e) {
+            R d[NV];
+            euler_dflux<R, M>(P0, W0, gm1, e, dW0[e], d);
+#pragma unroll
+            for (int b = 0; b < NV; ++b) W0t[b] -= d[b];
+        }
+        euler_dflux<R, M>(P0, W0, gm1, 0, W0t, FA0);
+        euler_flux<R, M>(P0, W0, 0, F0);
+    }
+    /* moments carrying the spatial slopes */
+    R FT0[NV], FTl[NV], FTr[NV], WTl[NV], WTr[NV];
+    psi_mom_T<R, M, 1>(T0, s0, FT0);
+    psi_mom_T<R, M, 1>(Tl, sl, FTl);
+    psi_mom_T<R, M, 1>(Tr, sr, FTr);
+    psi_mom_T<R, M, 0>(Tl, sl, WTl);
+    psi_mom_T<R, M, 0>(Tr, sr, WTr);
+
+    /* collision times and time integrals */
+    const R pl = Pl.p, pr = Pr.p;
+    const R tn = R(fp.c1) * dt + R(fp.c2) * RT<R>::abs_(pl - pr) / (pl + pr) * dt;
+    const R hdt = R(0.5) * dt;
+    R eh = R(0), e1 = R(0);
+    if (tn > R(0)) {
+        eh = RT<R>::exp_(-hdt / tn);
+        e1 = eh * eh; /* exp(-dt/tn) */
+    }
+    const R ie_h = tn * (R(1) - eh), ie_1 = tn * (R(1) - e1);
+    const R ite_h = tn * tn - tn * (hdt + tn) * eh, ite_1 = tn * tn - tn * (dt + tn) * e1;
+    const R idt = R(1) / dt;
+    const R cF1 = (R(4) * ie_h - ie_1) * idt, cF2 = (R(4) * ite_h - ite_1) * idt;
+    const R cT1 = R(4) * (ie_1 - R(2) * ie_h) * idt * idt, cT2 = R(4) * (ite_1 - R(2) * ite_h) * idt * idt;
+#pragma unroll
+    for (int b = 0; b < NV; ++b) {
+        const R dk = Fk[b] - F0[b];
+        const R dT = P0.rho * FT0[b] - (Pl.rho * FTl[b] + Pr.rho * FTr[b]);
+        F[b] = F0[b] + cF1 * dk + cF2 * dT;
+        Ft[b] = FA0[b] + cT1 * dk + cT2 * dT;
+        Wh[b] = W0[b] + hdt * (R(1) - eh) * W0t[b] - hdt * eh * (Pl.rho * WTl[b] + Pr.rho * WTr[b]);
+    }
+    return true;
+}
+
+} // namespace gks

@@ -1,0 +1,53 @@
+/* Internal host-side declarations of libgenogks (not part of the C ABI). */
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdio>
+
+#include "../../include/genogks.h"
+#include "kernels.cuh"
+
+struct gks_ctx {
+    int dim, nv, ng, precision, order;
+    int n[3];
+    double h, gamma;
+    gks_opts_t opts;
+    gks::KP kp;
+    cudaStream_t stream;
+    /* state and stage buffers (FP64) */
+    double *W, *G, *Ws, *Gs, *Acc;
+    /* device scalars */
+    double *dt;
+    unsigned long long *smax;
+    int *status;
+    /* reconstruction coefficients (multi-D) and face quantities, in the
+     * reconstruction precision */
+    void *B;
+    void *ff;
+    size_t B_elems, ff_elems;
+    /* all of the above live in one workspace */
+    void *ws;
+    size_t ws_bytes;
+    int own_ws;
+    /* lazily allocated staging buffer for host-side outputs */
+    double *stage_out;
+    size_t stage_bytes;
+    char err[256];
+};
+
+namespace gks {
+
+/* per-dimension launchers (k1d.cu, k2d.cu, k3d.cu) */
+template <int M> cudaError_t launch_states(gks_ctx *c, const double *W, const double *G, double *fs_dev);
+template <int M> cudaError_t launch_flux(gks_ctx *c, const double *W, const double *G);
+template <int M> cudaError_t launch_update(gks_ctx *c, int stage);
+template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl);
+
+inline int ngauss(int m) { return m == 1 ? 1 : (m == 2 ? 2 : 4); }
+inline int ncubic(int m) { return m == 2 ? GENO_NC2 : (m == 3 ? GENO_NC3 : 0); }
+
+constexpr int kBlock = 128;
+inline unsigned blocks_for(long n, int b = kBlock) { return (unsigned)((n + b - 1) / b); }
+
+} // namespace gks

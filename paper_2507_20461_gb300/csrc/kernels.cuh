@@ -1,0 +1,610 @@
+/*
+ * Kernels of one stage of the compact GKS with GENO reconstruction
+ * (arXiv 2507.20461, Sec. 2-4), templated on the dimension M and on the
+ * reconstruction/flux precision R (double, or float with FP64 accumulation).
+ *
+ * Stage pipeline on uniform grids (cell size h, nv = M + 2 variables):
+ *   1D   face1d        one thread per face: p^7 on {j-1..j+2} (shared by both
+ *                      sides), the three sub-stencil quadratics of each side,
+ *                      GENO blend, admissibility fallback, GKS flux.
+ *   M-D  cell_poly     one thread per cell (plus the ghost ring): least-squares
+ *                      cubic, linear sub-polynomials, GENO blend -> blended
+ *                      cubic coefficients B[v][k].
+ *        face_flux     one thread per (face, Gauss point) of one direction:
+ *                      both interface states from B, admissibility fallback,
+ *                      GKS flux, F / dF/dt / W(dt/2) to the face arrays.
+ *   all  update        one thread per cell: FP64 two-stage update of the
+ *                      averages (Eq. semifvs) and of the averaged gradients by
+ *                      the Gauss theorem (Eq. slope).
+ * Ghost cells are index mappings (periodic wrap, or transmissive even
+ * extension with the normal derivative negated); no padded copies exist.
+ */
+#pragma once
+#include <cstdint>
+
+#include "geno_coeffs.cuh"
+#include "gks_device.cuh"
+
+namespace gks {
+
+enum StatusBits : int { ST_RHO = 1, ST_P = 2, ST_NAN = 4, ST_FLUX = 8 };
+
+struct KP {
+    int n[3];
+    int bc;      /* 0 periodic, 1 transmissive */
+    int limiter; /* 0 GENO, 1 linear */
+    long ncell;
+    long nface[3];
+    long foff[3];
+    long nftot;
+    int ext[3]; /* extended box: n + 2 along the active axes */
+    long next;
+    double h, ih, gamma;
+    double C, itanhC, eps, C0, adm;
+    FluxParams fp;
+};
+
+__device__ __forceinline__ int map_idx(int i, int n, int bc, int &flip)
+{
+    if (i >= 0 && i < n) return i;
+    if (bc == 0) {
+        i %= n;
+        if (i < 0) i += n;
+        return i;
+    }
+    while (i < 0 || i >= n) {
+        if (i < 0) { i = -1 - i; flip ^= 1; }
+        if (i >= n) { i = 2 * n - 1 - i; flip ^= 1; }
+    }
+    return i;
+}
+
+/* linear cell index and the transmissive sign flips of a (ghost) cell */
+template <int M>
+__device__ __forceinline__ long cell_lin(const KP &P, int i, int j, int k, int *flip)
+{
+    flip[0] = flip[1] = flip[2] = 0;
+    const int ii = map_idx(i, P.n[0], P.bc, flip[0]);
+    const int jj = (M >= 2) ? map_idx(j, P.n[1], P.bc, flip[1]) : 0;
+    const int kk = (M >= 3) ? map_idx(k, P.n[2], P.bc, flip[2]) : 0;
+    return ((long)kk * P.n[1] + jj) * P.n[0] + ii;
+}
+
+template <typename R>
+__device__ __forceinline__ R chi_of(const KP &P, R ISt, R ISH, R ISL, int r)
+{
+    const R eps = R(P.eps);
+    R xH = ISt / (ISH + eps), xL = ISt / (ISL + eps);
+    R pH = xH * xH, pL = xL * xL;
+    if (r == 3) { pH *= xH; pL *= xL; }
+    const R aH = R(1) + pH, aL = R(1) + pL;
+    const R alpha = R(2) * aH / (aH + aL);
+    return RT<R>::tanh_(R(P.C) * alpha) * R(P.itanhC);
+}
+
+template <typename R, int M>
+__device__ __forceinline__ bool admissible(const R *w, const R *wc, R gm1, R delta)
+{
+    R ke = R(0), kc = R(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        ke += w[1 + a] * w[1 + a];
+        kc += wc[1 + a] * wc[1 + a];
+    }
+    if (!(w[0] > delta * wc[0])) return false;
+    const R p = gm1 * (w[M + 1] - R(0.5) * ke / w[0]);
+    const R pc = gm1 * (wc[M + 1] - R(0.5) * kc / wc[0]);
+    return p > delta * pc;
+}
+
+/* ------------------------------------------------------------------ */
+/* 1D: reconstruction + flux per face                                  */
+/* ------------------------------------------------------------------ */
+/* GENO blend of one side.  a[k][0..1] = (a1, a2) of the sub-stencil
+ * quadratics S1, S2 (central), S3 about the reconstruction cell; pv/pd =
+ * their values/derivatives at the face; qv/qd = p^7 at the face.  All in cell
+ * units relative to the reconstruction cell's average. */
+template <typename R>
+__device__ __forceinline__ void geno1d_blend(const KP &P, const R (*a)[2], const R *pv, const R *pd, R qv, R qd, R &val,
+                                             R &der)
+{
+    R IS[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) IS[k] = a[k][0] * a[k][0] + R(13.0 / 3.0) * a[k][1] * a[k][1];
+    const R ISH = fmax(IS[0], fmax(IS[1], IS[2]));
+    const R ISL = fmin(IS[0], fmin(IS[1], IS[2]));
+    const R ISt = RT<R>::abs_(R(0.5) * (IS[1] + IS[2]) - IS[0]);
+    const R chi = P.limiter ? R(1) : chi_of<R>(P, ISt, ISH, ISL, 2);
+    const R eps = R(P.eps);
+    const R w0 = R(1) / ((IS[0] + eps) * (IS[0] + eps));
+    const R w1 = R(P.C0) / ((IS[1] + eps) * (IS[1] + eps));
+    const R w2 = R(1) / ((IS[2] + eps) * (IS[2] + eps));
+    const R iws = R(1) / (w0 + w1 + w2);
+    const R lv = (w0 * pv[0] + w1 * pv[1] + w2 * pv[2]) * iws;
+    const R ld = (w0 * pd[0] + w1 * pd[1] + w2 * pd[2]) * iws;
+    val = chi * qv + (R(1) - chi) * lv;
+    der = chi * qd + (R(1) - chi) * ld;
+}
+
+/* states[side][v][c]: c = 0 value, 1 physical derivative */
+template <typename R>
+__device__ __forceinline__ void recon1d_face(const KP &P, const double *__restrict__ W, const double *__restrict__ G, int f,
+                                             R (*st)[3][2], R (*cw)[3])
+{
+    double w[4][3], d[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int flip[3];
+        const long c = cell_lin<1>(P, f - 2 + q, 0, 0, flip);
+        const double sg = flip[0] ? -P.h : P.h;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            w[q][v] = W[v * P.ncell + c];
+            d[q][v] = G[v * P.ncell + c] * sg;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        /* left: reconstruction cell j = f-1 (index 1), deltas relative to it */
+        const R wm1 = R(w[0][v] - w[1][v]), w1 = R(w[2][v] - w[1][v]), w2 = R(w[3][v] - w[1][v]);
+        R qv, qd;
+        p7_face<R>(wm1, R(0), w1, w2, R(d[0][v]), R(d[1][v]), R(d[2][v]), R(d[3][v]), qv, qd);
+        {
+            const R dm1 = R(d[0][v]);
+            R a[3][2], pv[3], pd[3];
+            a[0][1] = -(wm1 + dm1);
+            a[0][0] = -R(2) * wm1 - dm1;
+            a[1][0] = R(0.5) * (w1 - wm1);
+            a[1][1] = R(0.5) * (w1 + wm1);
+            a[2][1] = R(0.5) * (w2 - R(2) * w1);
+            a[2][0] = R(0.5) * (R(4) * w1 - w2);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                pv[k] = R(0.5) * a[k][0] + a[k][1] * R(1.0 / 6.0);
+                pd[k] = a[k][0] + a[k][1];
+            }
+            R val, der;
+            geno1d_blend<R>(P, a, pv, pd, qv, qd, val, der);
+            st[0][v][0] = R(w[1][v]) + val;
+            st[0][v][1] = der * R(P.ih);
+            cw[0][v] = R(w[1][v]);
+        }
+        /* right: reconstruction cell j+1 = f (index 2), mirrored stencils */
+        {
+            const R dj = R(w[2][v] - w[1][v]);
+            const R um2 = R(w[0][v] - w[2][v]), um1 = R(w[1][v] - w[2][v]), u1 = R(w[3][v] - w[2][v]);
+            const R d1 = R(d[3][v]);
+            R a[3][2], pv[3], pd[3];
+            a[0][1] = d1 - u1;
+            a[0][0] = R(2) * u1 - d1;
+            a[1][0] = R(0.5) * (u1 - um1);
+            a[1][1] = R(0.5) * (u1 + um1);
+            a[2][1] = R(0.5) * (um2 - R(2) * um1);
+            a[2][0] = R(0.5) * (um2 - R(4) * um1);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                pv[k] = -R(0.5) * a[k][0] + a[k][1] * R(1.0 / 6.0);
+                pd[k] = a[k][0] - a[k][1];
+            }
+            R val, der;
+            geno1d_blend<R>(P, a, pv, pd, qv - dj, qd, val, der);
+            st[1][v][0] = R(w[2][v]) + val;
+            st[1][v][1] = der * R(P.ih);
+            cw[1][v] = R(w[2][v]);
+        }
+    }
+}
+
+/* FLUX = false: write the interface states face_states[side][v][c][face] (double).
+ * FLUX = true : write ff[q][v][face] (R), q = F, dF/dt, W(dt/2). */
+template <typename R, bool FLUX>
+__global__ void __launch_bounds__(128) face1d_kernel(KP P, const double *__restrict__ W, const double *__restrict__ G,
+                                                     const double *__restrict__ dtp, double *__restrict__ fs,
+                                                     R *__restrict__ ff, int *__restrict__ status)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f > P.n[0]) return;
+    R st[2][3][2], cw[2][3];
+    recon1d_face<R>(P, W, G, f, st, cw);
+    const R gm1 = R(P.gamma - 1.0);
+    R Wl[3], Wr[3], dWl[1][3], dWr[1][3];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        R s[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) s[v] = st[side][v][0];
+        const bool ok = admissible<R, 1>(s, cw[side], gm1, R(P.adm));
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const R val = ok ? st[side][v][0] : cw[side][v];
+            const R der = ok ? st[side][v][1] : R(0);
+            if (side == 0) { Wl[v] = val; dWl[0][v] = der; }
+            else { Wr[v] = val; dWr[0][v] = der; }
+        }
+    }
+    if (!FLUX) {
+        const long nf = P.nftot;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            fs[((long)(0 * 3 + v) * 2 + 0) * nf + f] = (double)Wl[v];
+            fs[((long)(0 * 3 + v) * 2 + 1) * nf + f] = (double)dWl[0][v];
+            fs[((long)(1 * 3 + v) * 2 + 0) * nf + f] = (double)Wr[v];
+            fs[((long)(1 * 3 + v) * 2 + 1) * nf + f] = (double)dWr[0][v];
+        }
+        return;
+    }
+    R F[3], Ft[3], Wh[3];
+    const R dt = R(dtp[0]);
+    if (!gks_point<R, 1>(P.fp, dt, Wl, Wr, dWl, dWr, F, Ft, Wh)) {
+        atomicOr(status, ST_FLUX);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) F[v] = Ft[v] = Wh[v] = R(0);
+    }
+    const long nf = P.nftot;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        ff[(0 * 3 + v) * nf + f] = F[v];
+        ff[(1 * 3 + v) * nf + f] = Ft[v];
+        ff[(2 * 3 + v) * nf + f] = Wh[v];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* multi-D: blended GENO cubic per cell                                 */
+/* ------------------------------------------------------------------ */
+template <typename R, int M> struct Cubic;
+template <typename R> struct Cubic<R, 2> {
+    static constexpr int NC = GENO_NC2, ND = GENO_ND2;
+    __device__ __forceinline__ static void fit(const R *d, R *c) { cubic2d_fit<R>(d, c); }
+    __device__ __forceinline__ static void ind(const R *c, R &h, R &t) { cubic2d_indicators<R>(c, h, t); }
+};
+template <typename R> struct Cubic<R, 3> {
+    static constexpr int NC = GENO_NC3, ND = GENO_ND3;
+    __device__ __forceinline__ static void fit(const R *d, R *c) { cubic3d_fit<R>(d, c); }
+    __device__ __forceinline__ static void ind(const R *c, R &h, R &t) { cubic3d_indicators<R>(c, h, t); }
+};
+
+/* thread -> extended cell (-1..n along every active axis); false for corner
+ * cells (two or more ghost coordinates) that no face needs */
+template <int M>
+__device__ __forceinline__ bool ext_cell(const KP &P, long t, int &i, int &j, int &k)
+{
+    i = (int)(t % P.ext[0]) - 1;
+    j = (M >= 2) ? (int)((t / P.ext[0]) % P.ext[1]) - 1 : 0;
+    k = (M >= 3) ? (int)(t / ((long)P.ext[0] * P.ext[1])) - 1 : 0;
+    int out = (i < 0 || i >= P.n[0]);
+    if (M >= 2) out += (j < 0 || j >= P.n[1]);
+    if (M >= 3) out += (k < 0 || k >= P.n[2]);
+    return out <= 1;
+}
+
+template <typename R, int M>
+__global__ void __launch_bounds__(128) cell_poly_kernel(KP P, const double *__restrict__ W, const double *__restrict__ G,
+                                                        R *__restrict__ B)
+{
+    constexpr int NV = M + 2, NC = Cubic<R, M>::NC, ND = Cubic<R, M>::ND;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.next) return;
+    int i, j, k;
+    if (!ext_cell<M>(P, t, i, j, k)) return;
+    /* the seven (five) cells of the cross: own first, then q = 2 e + (side > 0) */
+    long cl[2 * M + 1];
+    int fl[2 * M + 1][3];
+    cl[0] = cell_lin<M>(P, i, j, k, fl[0]);
+#pragma unroll
+    for (int q = 0; q < 2 * M; ++q) {
+        int o[3] = {i, j, k};
+        o[q / 2] += (q & 1) ? 1 : -1;
+        cl[1 + q] = cell_lin<M>(P, o[0], o[1], o[2], fl[1 + q]);
+    }
+    const double h = P.h;
+#pragma unroll 1
+    for (int v = 0; v < NV; ++v) {
+        const double W0 = W[v * P.ncell + cl[0]];
+        R d[ND];
+#pragma unroll
+        for (int q = 0; q < 2 * M; ++q) {
+            d[q * (1 + M)] = R(W[v * P.ncell + cl[1 + q]] - W0);
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                const double g = G[(a * NV + v) * P.ncell + cl[1 + q]] * h;
+                d[q * (1 + M) + 1 + a] = R(fl[1 + q][a] ? -g : g);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            const double g = G[(a * NV + v) * P.ncell + cl[0]] * h;
+            d[2 * M * (1 + M) + a] = R(fl[0][a] ? -g : g);
+        }
+        R c[NC];
+        Cubic<R, M>::fit(d, c);
+        R chi = R(1), gb[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) gb[a] = R(0);
+        if (!P.limiter) {
+            R ISH, ISt;
+            Cubic<R, M>::ind(c, ISH, ISt);
+            /* linear sub-polynomials on {cell, neighbour q}: g_e = (s dW + D_e)/2, g_t = D_t */
+            R IS[2 * M], g[2 * M][M];
+#pragma unroll
+            for (int q = 0; q < 2 * M; ++q) {
+                const int e = q / 2;
+                const R s = (q & 1) ? R(1) : R(-1);
+                R sum = R(0);
+#pragma unroll
+                for (int a = 0; a < M; ++a) {
+                    const R D = d[q * (1 + M) + 1 + a];
+                    g[q][a] = (a == e) ? R(0.5) * (s * d[q * (1 + M)] + D) : D;
+                    sum += g[q][a] * g[q][a];
+                }
+                IS[q] = sum;
+            }
+            R smin = IS[0], smax = IS[0], ssum = R(0);
+#pragma unroll
+            for (int q = 0; q < 2 * M; ++q) {
+                smin = fmin(smin, IS[q]);
+                smax = fmax(smax, IS[q]);
+                ssum += IS[q];
+            }
+            const R ISL = (ssum - smin - smax) * R(1.0 / (2 * M - 2));
+            chi = chi_of<R>(P, ISt, ISH, ISL, 3);
+            const R eps = R(P.eps);
+            R ws = R(0);
+#pragma unroll
+            for (int q = 0; q < 2 * M; ++q) {
+                const R wq = R(1) / ((IS[q] + eps) * (IS[q] + eps));
+                ws += wq;
+#pragma unroll
+                for (int a = 0; a < M; ++a) gb[a] += wq * g[q][a];
+            }
+            const R iws = R(1) / ws;
+#pragma unroll
+            for (int a = 0; a < M; ++a) gb[a] *= iws;
+        }
+        /* blended cubic: chi c, plus (1 - chi) gbar on the linear monomials
+         * (coefficient M-1-a multiplies xi_a) */
+        const long base = (long)v * NC;
+#pragma unroll
+        for (int kk = 0; kk < NC; ++kk) {
+            R b = chi * c[kk];
+            if (kk < M) b += (R(1) - chi) * gb[M - 1 - kk];
+            B[(base + kk) * P.next + t] = b;
+        }
+    }
+}
+
+template <int M>
+__device__ __forceinline__ long ext_lin(const KP &P, int i, int j, int k)
+{
+    long r = i + 1;
+    if (M >= 2) r += (long)(j + 1) * P.ext[0];
+    if (M >= 3) r += (long)(k + 1) * P.ext[0] * P.ext[1];
+    return r;
+}
+
+/* one (face, Gauss point) of direction D.  FLUX = false writes the states
+ * face_states[side][v][c][g][face] (double, global axes); FLUX = true the
+ * fluxes ff[q][v][g][face] (R, global momentum order). */
+template <typename R, int M, int D, bool FLUX>
+__global__ void __launch_bounds__(128) face_flux_kernel(KP P, const double *__restrict__ W, const R *__restrict__ B,
+                                                        const double *__restrict__ dtp, double *__restrict__ fs,
+                                                        R *__restrict__ ff, int *__restrict__ status)
+{
+    constexpr int NV = M + 2, NC = Cubic<R, M>::NC, NG = (M == 2) ? 2 : 4;
+    const long nf = P.nface[D];
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nf * NG) return;
+    const int g = (int)(t / nf);
+    const long fl = t - (long)g * nf;
+    int e0 = P.n[0] + (D == 0), e1 = P.n[1] + (D == 1);
+    int idx[3];
+    idx[0] = (int)(fl % e0);
+    idx[1] = (M >= 2) ? (int)((fl / e0) % e1) : 0;
+    idx[2] = (M >= 3) ? (int)(fl / ((long)e0 * e1)) : 0;
+    const R gm1 = R(P.gamma - 1.0);
+    /* interface states, global axes: st[side][v][c], c = 0 value, 1 + e d/dx_e */
+    R st[2][NV][M + 1], cw[2][NV];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        int ci[3] = {idx[0], idx[1], idx[2]};
+        if (side == 0) ci[D] -= 1;
+        int flip[3];
+        const long cl = cell_lin<M>(P, ci[0], ci[1], ci[2], flip);
+        const long ce = ext_lin<M>(P, ci[0], ci[1], ci[2]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R c[NC], out[M + 1];
+#pragma unroll
+            for (int kk = 0; kk < NC; ++kk) c[kk] = B[((long)v * NC + kk) * P.next + ce];
+            if (side == 0) CubicEval<R, M, D, 1>::run(g, c, out);
+            else CubicEval<R, M, D, 0>::run(g, c, out);
+            const double w0 = W[v * P.ncell + cl];
+            cw[side][v] = R(w0);
+            st[side][v][0] = R(w0) + out[0];
+#pragma unroll
+            for (int a = 0; a < M; ++a) st[side][v][1 + a] = out[1 + a] * R(P.ih);
+        }
+        R s[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s[v] = st[side][v][0];
+        if (!admissible<R, M>(s, cw[side], gm1, R(P.adm))) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                st[side][v][0] = cw[side][v];
+#pragma unroll
+                for (int a = 0; a < M; ++a) st[side][v][1 + a] = R(0);
+            }
+        }
+    }
+    const long nft = P.nftot, face = P.foff[D] + fl;
+    if (!FLUX) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side)
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int c = 0; c < M + 1; ++c)
+                    fs[(((long)(side * NV + v) * (M + 1) + c) * NG + g) * nft + face] = (double)st[side][v][c];
+        return;
+    }
+    /* face frame: axis order (D, then the others ascending) */
+    constexpr int A1 = (D == 0) ? 1 : 0;
+    constexpr int A2 = (D == 2) ? 1 : 2;
+    const int ax[3] = {D, A1, A2};
+    R Wl[NV], Wr[NV], dWl[M][NV], dWr[M][NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        /* face-frame variable index fv of global variable v */
+        int fv = v;
+        if (v >= 1 && v <= M) {
+#pragma unroll
+            for (int kk = 0; kk < M; ++kk)
+                if (ax[kk] == v - 1) fv = 1 + kk;
+        }
+        Wl[fv] = st[0][v][0];
+        Wr[fv] = st[1][v][0];
+#pragma unroll
+        for (int kk = 0; kk < M; ++kk) {
+            dWl[kk][fv] = st[0][v][1 + ax[kk]];
+            dWr[kk][fv] = st[1][v][1 + ax[kk]];
+        }
+    }
+    R F[NV], Ft[NV], Wh[NV];
+    const R dt = R(dtp[0]);
+    if (!gks_point<R, M>(P.fp, dt, Wl, Wr, dWl, dWr, F, Ft, Wh)) {
+        atomicOr(status, ST_FLUX);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = Ft[v] = Wh[v] = R(0);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        int fv = v;
+        if (v >= 1 && v <= M) {
+#pragma unroll
+            for (int kk = 0; kk < M; ++kk)
+                if (ax[kk] == v - 1) fv = 1 + kk;
+        }
+        ff[((long)(0 * NV + v) * NG + g) * nft + face] = F[fv];
+        ff[((long)(1 * NV + v) * NG + g) * nft + face] = Ft[fv];
+        ff[((long)(2 * NV + v) * NG + g) * nft + face] = Wh[fv];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* FP64 stage update                                                   */
+/* ------------------------------------------------------------------ */
+template <int M>
+__device__ __forceinline__ long face_of(const KP &P, int d, int i, int j, int k, int s)
+{
+    int e0 = P.n[0] + (d == 0), e1 = P.n[1] + (d == 1);
+    int idx[3] = {i, j, k};
+    idx[d] += s;
+    return P.foff[d] + ((long)idx[2] * e1 + idx[1]) * e0 + idx[0];
+}
+
+/* STAGE 1: Ws = W - dt/2 L(F) - dt^2/8 L(Ft), Gs = Gauss(W(dt/2)), Acc = -dt L(F) - dt^2/6 L(Ft)
+ * STAGE 2: W += Acc - dt^2/3 L(Ft*),        G  = Gauss(W*(dt/2))
+ * with L(q)_j = (1/h) sum_d sum_g w_g (q(+d face) - q(-d face)). */
+template <typename R, int M, int STAGE>
+__global__ void __launch_bounds__(256) update_kernel(KP P, const R *__restrict__ ff, const double *__restrict__ dtp,
+                                                    double *__restrict__ W, double *__restrict__ G,
+                                                    double *__restrict__ Ws, double *__restrict__ Gs,
+                                                    double *__restrict__ Acc, int *__restrict__ status)
+{
+    constexpr int NV = M + 2, NG = (M == 1) ? 1 : ((M == 2) ? 2 : 4);
+    const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= P.ncell) return;
+    const int i = (int)(cell % P.n[0]);
+    const int j = (M >= 2) ? (int)((cell / P.n[0]) % P.n[1]) : 0;
+    const int k = (M >= 3) ? (int)(cell / ((long)P.n[0] * P.n[1])) : 0;
+    const double dt = dtp[0], ih = P.ih, wg = 1.0 / NG;
+    const long nft = P.nftot;
+    long fp[M], fm[M];
+#pragma unroll
+    for (int d = 0; d < M; ++d) {
+        fp[d] = face_of<M>(P, d, i, j, k, 1);
+        fm[d] = face_of<M>(P, d, i, j, k, 0);
+    }
+    double Wn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double DF = 0.0, DFt = 0.0;
+#pragma unroll
+        for (int d = 0; d < M; ++d) {
+            double Dh = 0.0;
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+                const long o0 = ((long)(0 * NV + v) * NG + g) * nft, o1 = ((long)(1 * NV + v) * NG + g) * nft,
+                           o2 = ((long)(2 * NV + v) * NG + g) * nft;
+                DF += (double)ff[o0 + fp[d]] - (double)ff[o0 + fm[d]];
+                DFt += (double)ff[o1 + fp[d]] - (double)ff[o1 + fm[d]];
+                Dh += (double)ff[o2 + fp[d]] - (double)ff[o2 + fm[d]];
+            }
+            double *Gout = (STAGE == 1) ? Gs : G;
+            Gout[(d * NV + v) * P.ncell + cell] = Dh * wg * ih;
+        }
+        DF *= wg * ih;
+        DFt *= wg * ih;
+        if (STAGE == 1) {
+            Ws[v * P.ncell + cell] = W[v * P.ncell + cell] - 0.5 * dt * DF - dt * dt * 0.125 * DFt;
+            Acc[v * P.ncell + cell] = -dt * DF - dt * dt / 6.0 * DFt;
+            Wn[v] = Ws[v * P.ncell + cell];
+        } else {
+            const double w = W[v * P.ncell + cell] + Acc[v * P.ncell + cell] - dt * dt / 3.0 * DFt;
+            W[v * P.ncell + cell] = w;
+            Wn[v] = w;
+        }
+    }
+    double ke = 0.0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) ke += Wn[1 + a] * Wn[1 + a];
+    const double p = (P.gamma - 1.0) * (Wn[M + 1] - 0.5 * ke / Wn[0]);
+    int st = 0;
+    if (!(Wn[0] > 0.0)) st |= ST_RHO;
+    if (!(p > 0.0)) st |= ST_P;
+    if (!isfinite(p) || !isfinite(Wn[0])) st |= ST_NAN;
+    if (st) atomicOr(status, st);
+}
+
+/* ------------------------------------------------------------------ */
+/* CFL time step on the device                                         */
+/* ------------------------------------------------------------------ */
+template <int M>
+__global__ void wavespeed_kernel(KP P, const double *__restrict__ W, unsigned long long *__restrict__ smax)
+{
+    double s = 0.0;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += (long)gridDim.x * blockDim.x) {
+        const double rho = W[c];
+        double ke = 0.0, um = 0.0;
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            const double u = W[(1 + a) * P.ncell + c] / rho;
+            ke += u * u;
+            um = fmax(um, fabs(u));
+        }
+        const double p = (P.gamma - 1.0) * (W[(M + 1) * P.ncell + c] - 0.5 * rho * ke);
+        s = fmax(s, um + sqrt(P.gamma * p / rho));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        /* non-negative doubles order like their bit patterns; NaN is caught on the host */
+        if (threadIdx.x == 0) atomicMax(smax, (unsigned long long)__double_as_longlong(isnan(s) ? 1e300 : s));
+    }
+}
+
+static __global__ void dt_from_speed_kernel(const unsigned long long *__restrict__ smax, double cfl_h, double *__restrict__ dtp)
+{
+    const double s = __longlong_as_double((long long)*smax);
+    dtp[0] = cfl_h / s;
+}
+
+static __global__ void set_scalar_kernel(double *__restrict__ p, double v) { p[0] = v; }
+
+} // namespace gks

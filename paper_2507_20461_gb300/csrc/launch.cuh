@@ -1,0 +1,85 @@
+/* Launch wrappers of the stage kernels for one dimension M; included by the
+ * per-dimension translation units k1d.cu, k2d.cu, k3d.cu. */
+#pragma once
+#include "internal.h"
+
+namespace gks {
+
+template <typename R, int M>
+static cudaError_t flux_impl(gks_ctx *c, const double *W, const double *G, double *fs_dev, bool flux)
+{
+    const KP &P = c->kp;
+    R *ff = (R *)c->ff;
+    if constexpr (M == 1) {
+        const unsigned nb = blocks_for(P.n[0] + 1);
+        if (flux) face1d_kernel<R, true><<<nb, kBlock, 0, c->stream>>>(P, W, G, c->dt, nullptr, ff, c->status);
+        else face1d_kernel<R, false><<<nb, kBlock, 0, c->stream>>>(P, W, G, c->dt, fs_dev, nullptr, c->status);
+    } else {
+        constexpr int NG = (M == 2) ? 2 : 4;
+        R *B = (R *)c->B;
+        cell_poly_kernel<R, M><<<blocks_for(P.next), kBlock, 0, c->stream>>>(P, W, G, B);
+        for (int d = 0; d < M; ++d) {
+            const unsigned nb = blocks_for(P.nface[d] * NG);
+#define GKS_FACE(D)                                                                                           \
+    if (d == D) {                                                                                             \
+        if (flux) face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, W, B, c->dt, nullptr, ff, c->status); \
+        else face_flux_kernel<R, M, D, false><<<nb, kBlock, 0, c->stream>>>(P, W, B, c->dt, fs_dev, nullptr, c->status); \
+    }
+            GKS_FACE(0)
+            GKS_FACE(1)
+            if constexpr (M == 3) { GKS_FACE(2) }
+#undef GKS_FACE
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <int M> cudaError_t launch_states(gks_ctx *c, const double *W, const double *G, double *fs_dev)
+{
+    return c->precision ? flux_impl<float, M>(c, W, G, fs_dev, false) : flux_impl<double, M>(c, W, G, fs_dev, false);
+}
+
+template <int M> cudaError_t launch_flux(gks_ctx *c, const double *W, const double *G)
+{
+    return c->precision ? flux_impl<float, M>(c, W, G, nullptr, true) : flux_impl<double, M>(c, W, G, nullptr, true);
+}
+
+template <typename R, int M> static cudaError_t update_impl(gks_ctx *c, int stage)
+{
+    const KP &P = c->kp;
+    const unsigned nb = blocks_for(P.ncell, 256);
+    const R *ff = (const R *)c->ff;
+    if (stage == 1)
+        update_kernel<R, M, 1><<<nb, 256, 0, c->stream>>>(P, ff, c->dt, c->W, c->G, c->Ws, c->Gs, c->Acc, c->status);
+    else
+        update_kernel<R, M, 2><<<nb, 256, 0, c->stream>>>(P, ff, c->dt, c->W, c->G, c->Ws, c->Gs, c->Acc, c->status);
+    return cudaGetLastError();
+}
+
+template <int M> cudaError_t launch_update(gks_ctx *c, int stage)
+{
+    return c->precision ? update_impl<float, M>(c, stage) : update_impl<double, M>(c, stage);
+}
+
+template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl)
+{
+    cudaError_t e = cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    long want = (c->kp.ncell + 255) / 256;
+    long cap = (long)nsm * 8;
+    const unsigned nb = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+    wavespeed_kernel<M><<<nb, 256, 0, c->stream>>>(c->kp, c->W, c->smax);
+    if (cfl > 0.0) dt_from_speed_kernel<<<1, 1, 0, c->stream>>>(c->smax, cfl * c->h, c->dt);
+    return cudaGetLastError();
+}
+
+#define GKS_INSTANTIATE(M)                                                                                \
+    template cudaError_t launch_states<M>(gks_ctx *, const double *, const double *, double *);          \
+    template cudaError_t launch_flux<M>(gks_ctx *, const double *, const double *);                      \
+    template cudaError_t launch_update<M>(gks_ctx *, int);                                                \
+    template cudaError_t launch_wavespeed<M>(gks_ctx *, double);
+
+} // namespace gks

@@ -1,0 +1,326 @@
+"""Parity of the CUDA library (through its C ABI) with the oracle, on cuda:0.
+
+Bars (tolerances written here, derived in the design doc):
+  - FP64 interface states and fluxes: element-wise, relative 1e-12 of the
+    variable's scale (values) and 1e-10 (derivatives, time derivatives);
+  - FP64 one step: per-variable relative L1 residual <= 1e-12;
+  - FP64 after a full run: relative L1 <= 1e-9 per variable;
+  - mixed precision (FP32 reconstruction/flux, FP64 accumulation): mean
+    |rho_gpu - rho_oracle| <= 1e-5.
+Sizes span several thread blocks and a ragged tail; the full-size cases use
+the launch path the benchmark times (gks_step_cfl) and compare sampled
+windows, whose centres depend on nothing outside the window.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2507_20461_gb300 import binding as B
+from paper_2507_20461_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def _random_smooth(dim, n, seed, bc):
+    """Smooth state with a random perturbation of the averages and gradients."""
+    rng = np.random.default_rng(seed)
+    W, G, h = I.sine_wave(dim, n[0]) if len(set(n)) == 1 else (None, None, None)
+    shape = tuple(reversed(n))
+    h = 1.0 / n[0]
+    grids = np.meshgrid(*[(np.arange(k) + 0.5) * h for k in reversed(n)], indexing="ij")
+    phase = sum((a + 1) * g for a, g in enumerate(reversed(grids)))
+    rho = 1.0 + 0.3 * np.sin(2 * math.pi * phase) + 0.05 * rng.random(shape)
+    vel = [0.3 * np.cos(2 * math.pi * (phase + 0.1 * a)) + 0.05 * rng.random(shape) for a in range(dim)]
+    p = 1.0 + 0.2 * np.cos(2 * math.pi * phase) + 0.05 * rng.random(shape)
+    ke = sum(u * u for u in vel)
+    W = np.stack([rho] + [rho * u for u in vel] + [p / 0.4 + 0.5 * rho * ke])
+    G = 0.5 * rng.normal(size=(dim,) + W.shape)
+    return W, G, h
+
+
+def _solver(dim, n, h, bc, precision=0, **kw):
+    hi = [k * h for k in n]
+    return B.Solver(tuple(n), lo=[0.0] * dim, hi=hi, gamma=1.4, bc=bc, precision=precision, **kw)
+
+
+CASES = [
+    (1, (53,)),
+    (2, (37, 29)),
+    (3, (11, 9, 7)),
+]
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("dim,n", CASES)
+def test_reconstruct_parity(dim, n, bc):
+    W, G, h = _random_smooth(dim, n, 1 + dim, bc)
+    cfg = O.make_cfg(dim, n, h, bc=bc)
+    ref = O.reconstruct(cfg, W, G)
+    s = _solver(dim, n, h, bc)
+    s.set_state(_dev(W), _dev(G))
+    out = torch.zeros(ref.size, dtype=torch.float64, device=DEV)
+    s.reconstruct(out)
+    got = out.cpu().numpy().reshape(ref.shape)
+    nv = dim + 2
+    for v in range(nv):
+        scale = np.abs(W[v]).max() + 1e-300
+        np.testing.assert_allclose(got[:, v, 0], ref[:, v, 0], rtol=0, atol=1e-12 * scale)
+        dscale = np.abs(ref[:, v, 1:]).max() + scale / h
+        np.testing.assert_allclose(got[:, v, 1:], ref[:, v, 1:], rtol=0, atol=1e-11 * dscale)
+    s.close()
+
+
+@pytest.mark.parametrize("dim,n", CASES)
+def test_flux_parity(dim, n):
+    bc = 1
+    W, G, h = _random_smooth(dim, n, 10 + dim, bc)
+    cfg = O.make_cfg(dim, n, h, bc=bc)
+    dt = 0.3 * h / O.max_wavespeed(cfg, W)
+    ref = O.flux(cfg, dt, W, G)
+    s = _solver(dim, n, h, bc)
+    s.set_state(_dev(W), _dev(G))
+    out = torch.zeros(ref.size, dtype=torch.float64, device=DEV)
+    s.flux(dt, out)
+    got = out.cpu().numpy().reshape(ref.shape)
+    for v in range(dim + 2):
+        Fs = np.abs(ref[0, v]).max() + 1e-300
+        np.testing.assert_allclose(got[0, v], ref[0, v], rtol=0, atol=1e-12 * Fs)
+        # dF/dt: recovered from time integrals, oracle rounding ~ eps |F| / dt
+        np.testing.assert_allclose(got[1, v], ref[1, v], rtol=0, atol=1e-10 * (np.abs(ref[1, v]).max() + Fs / dt))
+        np.testing.assert_allclose(got[2, v], ref[2, v], rtol=0, atol=1e-12 * (np.abs(ref[2, v]).max() + 1e-300))
+    s.close()
+
+
+def _rel_l1(a, b):
+    nv = a.shape[0]
+    return np.array([np.abs(a[v] - b[v]).sum() / (np.abs(b[v]).sum() + 1e-300) for v in range(nv)])
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("dim,n", CASES)
+def test_one_step_parity(dim, n, bc):
+    W, G, h = _random_smooth(dim, n, 20 + dim, bc)
+    cfg = O.make_cfg(dim, n, h, bc=bc)
+    dt = 0.4 * h / O.max_wavespeed(cfg, W)
+    Wo, Go = W.copy(), G.copy()
+    assert O.step(cfg, dt, Wo, Go) == 0
+    s = _solver(dim, n, h, bc)
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    s.step(dt)
+    s.get_state(Wd, Gd)
+    Wg, Gg = Wd.cpu().numpy(), Gd.cpu().numpy()
+    assert _rel_l1(Wg, Wo).max() <= 1e-12
+    for d in range(dim):
+        np.testing.assert_allclose(Gg[d], Go[d], rtol=0, atol=1e-9 * np.abs(Go[d]).max())
+    s.close()
+
+
+def _run_pair(dim, n, h, bc, W, G, nsteps, cfl=0.4, precision=0):
+    """nsteps on both sides with the oracle's CFL time steps fed to the GPU."""
+    cfg = O.make_cfg(dim, n, h, bc=bc)
+    s = _solver(dim, n, h, bc, precision=precision)
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    Wo, Go = W.copy(), G.copy()
+    for _ in range(nsteps):
+        dt = cfl * h / O.max_wavespeed(cfg, Wo)
+        assert O.step(cfg, dt, Wo, Go) == 0
+        s.step(dt)
+    s.get_state(Wd, Gd)
+    out = (Wd.cpu().numpy(), Gd.cpu().numpy(), Wo, Go)
+    s.close()
+    return out
+
+
+def test_config1_full_run_parity():
+    """1D Euler, gamma 1.4, N = 400 on [0, 1], seeded two-state Riemann IC,
+    transmissive, CFL 0.4, 200 steps: relative L1 <= 1e-9 per variable."""
+    n = 400
+    W, G, h, _ = I.riemann_1d(n, seed=20461)
+    Wg, Gg, Wo, Go = _run_pair(1, (n,), h, 1, W, G, 200)
+    assert _rel_l1(Wg, Wo).max() <= 1e-9
+
+
+def test_2d_quadrants_multistep_parity():
+    """Config-2-type four-quadrant IC (transmissive) on a ragged 45 x 38 grid, 25 steps."""
+    W, G, h = I.quadrants_2d(38, seed=20462, nx=45)
+    Wg, Gg, Wo, Go = _run_pair(2, (45, 38), h, 1, W, G, 25)
+    assert _rel_l1(Wg, Wo).max() <= 1e-9
+
+
+def test_3d_multistep_parity():
+    W, G, h = I.turbulence_3d(12, seed=20465)
+    Wg, Gg, Wo, Go = _run_pair(3, (12, 12, 12), h, 0, W, G, 4)
+    assert _rel_l1(Wg, Wo).max() <= 1e-10
+
+
+@pytest.mark.parametrize("dim,n,seed", [(2, (64, 64), 20463), (1, (200,), 20461)])
+def test_mixed_precision_density_l1(dim, n, seed):
+    """FP32 reconstruction/flux with FP64 accumulation against the FP64 oracle."""
+    if dim == 2:
+        W, G, h = I.fourier_shocks_2d(n[0], seed=seed)
+        bc = 0
+    else:
+        W, G, h, _ = I.riemann_1d(n[0], seed=seed)
+        bc = 1
+    Wg, Gg, Wo, Go = _run_pair(dim, n, h, bc, W, G, 20, precision=1)
+    err = np.abs(Wg[0] - Wo[0]).mean()
+    assert err <= 1e-5, err
+
+
+def _window_check(Wfull, Gfull, Wnew, Gnew, dim, n, h, dt, rng, nwin=6, r=4, pad=4, tol=1e-12):
+    """Oracle step on (2(r+pad)+1)^dim windows around random cells of a periodic
+    grid; the centre (radius pad... 0) is exact because a step reaches r cells."""
+    w = 2 * (r + pad) + 1
+    for _ in range(nwin):
+        c = [int(rng.integers(0, k)) for k in n]
+        idx = [np.arange(ci - r - pad, ci + r + pad + 1) % k for ci, k in zip(c, n)]
+        sl = np.ix_(*reversed(idx))
+        Ww = np.ascontiguousarray(Wfull[(slice(None),) + sl])
+        Gw = np.ascontiguousarray(Gfull[(slice(None), slice(None)) + sl])
+        cfg = O.make_cfg(dim, (w,) * dim, h, bc=1)
+        assert O.step(cfg, dt, Ww, Gw) == 0
+        ctr = (r + pad,) * dim
+        ref_w = Ww[(slice(None),) + ctr]
+        got_w = Wnew[(slice(None),) + tuple(reversed(c))]
+        np.testing.assert_allclose(got_w, ref_w, rtol=tol, atol=tol)
+        ref_g = Gw[(slice(None), slice(None)) + ctr]
+        got_g = Gnew[(slice(None), slice(None)) + tuple(reversed(c))]
+        np.testing.assert_allclose(got_g, ref_g, rtol=1e-9, atol=1e-9 * (np.abs(ref_g).max() + 1))
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
+def test_config3_full_size_sampled(precision, tol):
+    """2D 2048^2 periodic Fourier modes + 4 shocks (the benchmark workload),
+    one step through gks_step_cfl (dt computed on the device); sampled windows
+    compared with the oracle."""
+    n = 2048
+    W, G, h = I.fourier_shocks_2d(n, seed=20463)
+    s = _solver(2, (n, n), h, 0, precision=precision)
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    smax = s.max_wavespeed()
+    cfg = O.make_cfg(2, (8, 8), h)
+    dt = 0.4 * h / smax
+    s.step_cfl(0.4, 1)
+    s.get_state(Wd, Gd)
+    Wn, Gn = Wd.cpu().numpy(), Gd.cpu().numpy()
+    rng = np.random.default_rng(5)
+    _window_check(W, G, Wn, Gn, 2, (n, n), h, dt, rng, tol=tol)
+    s.close()
+
+
+def test_config2_full_size_sampled():
+    """2D 512^2 four-quadrant IC (transmissive), one FP64 step at full size, windows
+    away from the boundary compared with the oracle; plus 100 steps stay admissible."""
+    n = 512
+    W, G, h = I.quadrants_2d(n, seed=20462)
+    s = _solver(2, (n, n), h, 1)
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    dt = 0.4 * h / s.max_wavespeed()
+    s.step(dt)
+    s.get_state(Wd, Gd)
+    Wn, Gn = Wd.cpu().numpy(), Gd.cpu().numpy()
+    rng = np.random.default_rng(6)
+    # windows around the quadrant corner and interfaces (all interior, >= 9 cells from the edge)
+    for c in ([256, 256], [255, 300], [100, 256], [256, 40], [300, 470]):
+        r, pad = 4, 4
+        idx = [np.arange(ci - r - pad, ci + r + pad + 1) for ci in c]
+        sl = np.ix_(idx[1], idx[0])
+        Ww = np.ascontiguousarray(W[(slice(None),) + sl])
+        Gw = np.ascontiguousarray(G[(slice(None), slice(None)) + sl])
+        cfg = O.make_cfg(2, (17, 17), h, bc=1)
+        assert O.step(cfg, dt, Ww, Gw) == 0
+        np.testing.assert_allclose(Wn[:, c[1], c[0]], Ww[:, 8, 8], rtol=1e-12, atol=1e-12)
+    s.step_cfl(0.4, 100)
+    assert s.status() == 0
+    s.close()
+
+
+def test_free_stream_preserved():
+    for dim, n in CASES:
+        h = 1.0 / n[0]
+        shape = tuple(reversed(n))
+        W = np.zeros((dim + 2,) + shape)
+        W[0] = 1.3
+        for a in range(dim):
+            W[1 + a] = 1.3 * (0.2 + 0.1 * a)
+        W[dim + 1] = 2.0 / 0.4 + 0.5 * 1.3 * sum((0.2 + 0.1 * a) ** 2 for a in range(dim))
+        G = np.zeros((dim,) + W.shape)
+        s = _solver(dim, n, h, 0)
+        Wd, Gd = _dev(W), _dev(G)
+        s.set_state(Wd, Gd)
+        for _ in range(3):
+            s.step(0.2 * h)
+        s.get_state(Wd, Gd)
+        np.testing.assert_allclose(Wd.cpu().numpy(), W, rtol=1e-14, atol=1e-14)
+        assert np.abs(Gd.cpu().numpy()).max() < 1e-12
+        s.close()
+
+
+def test_periodic_conservation_gpu():
+    n = (64, 48)
+    W, G, h = _random_smooth(2, n, 31, 0)
+    s = _solver(2, n, h, 0)
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    s.step_cfl(0.4, 20)
+    s.get_state(Wd, Gd)
+    Wg = Wd.cpu().numpy()
+    np.testing.assert_allclose(Wg.sum(axis=(1, 2)), W.sum(axis=(1, 2)), rtol=1e-13)
+    s.close()
+
+
+def test_tiny_grids():
+    """Degenerate sizes: single-cell and two-cell axes run and agree with the oracle."""
+    for dim, n, bc in [(1, (2,), 0), (1, (1,), 1), (2, (1, 5), 0), (2, (3, 2), 1), (3, (2, 1, 3), 1)]:
+        W, G, h = _random_smooth(dim, n, 40, bc)
+        G *= 0.1
+        cfg = O.make_cfg(dim, n, h, bc=bc)
+        dt = 0.2 * h / O.max_wavespeed(cfg, W)
+        Wo, Go = W.copy(), G.copy()
+        assert O.step(cfg, dt, Wo, Go) == 0
+        s = _solver(dim, n, h, bc)
+        Wd, Gd = _dev(W), _dev(G)
+        s.set_state(Wd, Gd)
+        s.step(dt)
+        s.get_state(Wd, Gd)
+        assert _rel_l1(Wd.cpu().numpy(), Wo).max() <= 1e-12, (dim, n, bc)
+        s.close()
+
+
+def test_nonphysical_state_reported():
+    n = (16, 16)
+    W, G, h = _random_smooth(2, n, 50, 0)
+    W[3, 5, 5] = 0.1 * W[3, 5, 5] - 10.0  # negative pressure in one cell
+    s = _solver(2, n, h, 0)
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    s.step(1e-4)
+    with pytest.raises(B.GksError) as e:
+        s.get_state(Wd, Gd)
+    assert e.value.code == B.ERR_NONPHYSICAL
+    s.close()
+
+
+def test_bad_arguments():
+    s = _solver(2, (8, 8), 1.0 / 8, 0)
+    with pytest.raises(B.GksError) as e:
+        s.step(-1.0)
+    assert e.value.code == B.ERR_ARG
+    with pytest.raises(B.GksError) as e:
+        s.step(float("nan"))
+    assert e.value.code == B.ERR_ARG
+    s.close()
