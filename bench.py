@@ -1,0 +1,386 @@
+"""Benchmark: cell-updates/s of the compact GKS with GENO reconstruction on the
+2D 2048^2 periodic workload (16 random-phase density modes + 4 planar shocks,
+Mach 1.5-3), mixed precision (FP32 reconstruction/flux, FP64 accumulation)
+against FP64, with the L1 density error of mixed against FP64.
+
+One JSON line on rank 0.  A step is one full two-stage step of every cell
+(gks_step_cfl: device time step, stage 1, stage 2).  `value` is the mixed-
+precision device-timed rate; `fp64` holds the FP64 path's; `e2e` is the same
+metric through the C ABI with host buffers (state copied in from pinned host
+memory and read back every step).  `--impl reference` times the oracle (the
+plain CPU implementation) on the host cores instead.
+Multi-GPU: replicas only (independent grids per rank, no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 2048
+SEED = 20463
+CFL = 0.4
+METRIC = "cell-updates/s and % HBM roofline, 2D 2048² mixed vs FP64, at stated L1 err"
+WORKLOAD = "2D Euler 2048x2048 periodic, 16 random-phase density modes (k<=8) + 4 planar shocks Mach U[1.5,3], CFL 0.4"
+
+# Algorithmic work per unit of the dominant kernel (face_flux_kernel), counted
+# by ncu (2 x FMA + ADD + MUL instructions of the pipe) on a 256^2 case in
+# which every face Gauss point is evaluated exactly once:
+#   mixed path: 2004 FP32 flops per face Gauss point;
+#   FP64 path:  2368 FP64 flops per face Gauss point.
+FLOPS_PER_FACE_GP = {"mixed": 2004.0, "fp64": 2368.0}
+# Algorithmic HBM bytes per cell-update of the whole step (FP64 state,
+# stage buffers, accumulator), 2D: 60 doubles.
+BYTES_PER_CELL_UPDATE = 480.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "samples": len(sm),
+        }
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(n_sample: int = 256, steps: int = 2):
+    """The oracle (FP64, OpenMP over all host cores) on a bounded sample of the
+    workload: the same IC recipe on an n_sample^2 periodic grid."""
+    import oracle
+    from paper_2507_20461_gb300 import inputs as I
+
+    W, G, h = I.fourier_shocks_2d(n_sample, SEED)
+    cfg = oracle.make_cfg(2, (n_sample, n_sample), h, bc=0)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dt = CFL * h / oracle.max_wavespeed(cfg, W)
+        r = oracle.step(cfg, dt, W, G)
+        if r != 0:
+            raise RuntimeError(f"oracle step failed: {r}")
+    el = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {
+        "value": n_sample * n_sample * steps / el,
+        "unit": "cell-updates/s",
+        "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+        "kind": "oracle",
+        "sample": f"{n_sample}x{n_sample} periodic grid of the same IC recipe, {steps} FP64 steps (wall {el:.1f} s)",
+    }
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2507_20461_gb300 import inputs as I
+
+    n_sample = 192
+    W, G, h = I.fourier_shocks_2d(n_sample, SEED)
+    cfg = oracle.make_cfg(2, (n_sample, n_sample), h, bc=0)
+    for _ in range(args.warmup):
+        oracle.step(cfg, CFL * h / oracle.max_wavespeed(cfg, W), W, G)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.step(cfg, CFL * h / oracle.max_wavespeed(cfg, W), W, G)
+        if r != 0:
+            raise RuntimeError(f"oracle step failed: {r}")
+    el = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    value = n_sample * n_sample * args.steps / el
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{n_sample}x{n_sample} of the same IC recipe", "n": n_sample},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                          "sample": f"{n_sample}x{n_sample} periodic grid of the same IC recipe, one FP64 step per timed step"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_path(B, torch, W, G, h, precision, steps, warmup, dev):
+    """Device-timed steps of one precision; returns (ms/step, profile, final density)."""
+    stream = torch.cuda.current_stream()
+    s = B.Solver((N, N), bc=B.BC_PERIODIC, precision=precision, stream=stream)
+    Wd = torch.from_numpy(W).to(dev)
+    Gd = torch.from_numpy(G).to(dev)
+    s.set_state(Wd, Gd)
+    s.step_cfl(CFL, warmup)
+    torch.cuda.synchronize()
+    s.profile(True, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step_cfl(CFL, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = {k: s.profile_read(k) for k in (B.KC_RECON, B.KC_FACE, B.KC_UPDATE, B.KC_DT)}
+    s.profile(False, False)
+    st = s.status()
+    s.get_state(Wd, Gd)
+    rho = Wd[0].clone()
+    s.close()
+    return ms, prof, rho, st
+
+
+def time_e2e(B, torch, W, G, precision, steps, warmup, dev):
+    """Same metric through the C ABI with host buffers: each step copies the
+    state in from pinned host memory, steps, and reads the state back."""
+    stream = torch.cuda.current_stream()
+    s = B.Solver((N, N), bc=B.BC_PERIODIC, precision=precision, stream=stream)
+    Wh = torch.from_numpy(W).pin_memory()
+    Gh = torch.from_numpy(G).pin_memory()
+    Wo = torch.empty_like(Wh).pin_memory()
+    Go = torch.empty_like(Gh).pin_memory()
+    for _ in range(warmup):
+        s.set_state(Wh, Gh)
+        s.step_cfl(CFL, 1)
+        s.get_state(Wo, Go)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.set_state(Wh, Gh)
+        s.step_cfl(CFL, 1)
+        s.get_state(Wo, Go)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    s.close()
+    nbytes = Wh.numel() * 8 + Gh.numel() * 8
+    return N * N * steps / el, nbytes, nbytes
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2507_20461_gb300 import binding as B
+    from paper_2507_20461_gb300 import inputs as I
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    B.lib()
+
+    W, G, h = I.fourier_shocks_2d(N, SEED)
+    W = np.ascontiguousarray(W)
+    G = np.ascontiguousarray(G)
+
+    # FP64 path: fewer steps (about 10x slower), same warm-up rule
+    steps64 = max(2, min(args.steps, 5))
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms_mixed, prof_mixed, rho_mixed, st_mixed = time_path(B, torch, W, G, h, 1, args.steps, args.warmup, dev)
+    ms_fp64, prof_fp64, rho_fp64, st_fp64 = time_path(B, torch, W, G, h, 0, steps64, args.warmup, dev)
+    torch.cuda.synchronize()
+    if ws > 1:
+        t = torch.tensor([ms_mixed, ms_fp64], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_mixed, ms_fp64 = t.tolist()
+    clk = clocks.stop()
+
+    # mixed vs FP64 after the same number of steps (warmup + steps for each)
+    l1 = None
+    if args.steps + args.warmup == steps64 + args.warmup:
+        l1 = float((rho_mixed - rho_fp64).abs().mean())
+    else:
+        # equal-step comparison on a separate short run
+        s1 = B.Solver((N, N), bc=B.BC_PERIODIC, precision=1)
+        s0 = B.Solver((N, N), bc=B.BC_PERIODIC, precision=0)
+        Wd1, Gd1 = torch.from_numpy(W).to(dev), torch.from_numpy(G).to(dev)
+        Wd0, Gd0 = Wd1.clone(), Gd1.clone()
+        s1.set_state(Wd1, Gd1)
+        s0.set_state(Wd0, Gd0)
+        for _ in range(steps64 + args.warmup):
+            dt = CFL * h / s0.max_wavespeed()
+            s0.step(dt)
+            s1.step(dt)
+        s1.get_state(Wd1, Gd1)
+        s0.get_state(Wd0, Gd0)
+        l1 = float((Wd1[0] - Wd0[0]).abs().mean())
+        l1_steps = steps64 + args.warmup
+        s1.close()
+        s0.close()
+
+    e2e_val, h2d, d2h = time_e2e(B, torch, W, G, 1, max(2, min(args.steps, 5)), 1, dev)
+
+    peaks, peak_src = _peaks()
+    sm_clock = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    # FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = nsm * 128 * 2 * sm_clock * 1e6 / 1e12
+    # FP64 ALU peak: 2 DFMA per SM per clock (measured by a DFMA probe: 1.25 TFLOP/s at 2070 MHz)
+    fp64_peak = nsm * 2 * 2 * sm_clock * 1e6 / 1e12
+
+    def face_gps():
+        return 2 * (N + 1) * N * 2  # faces of both directions x 2 Gauss points
+
+    n_face, t_face = prof_mixed[B.KC_FACE]
+    # one face-flux launch per direction: units per launch = faces of one direction x 2 Gauss points
+    avg_face_ms = t_face / max(n_face, 1)
+    units_per_launch = (N + 1) * N * 2
+    achieved = FLOPS_PER_FACE_GP["mixed"] * units_per_launch / (avg_face_ms * 1e-3) / 1e12
+    n64, t64 = prof_fp64[B.KC_FACE]
+    avg64 = t64 / max(n64, 1)
+    achieved64 = FLOPS_PER_FACE_GP["fp64"] * units_per_launch / (avg64 * 1e-3) / 1e12
+
+    launches_per_step = 1 + 1 + 2 * (1 + 2 + 1)  # wavespeed, dt, 2 x (poly, 2 face dirs, update)
+    value = ws * N * N / (ms_mixed * 1e-3)
+    value64 = ws * N * N / (ms_fp64 * 1e-3)
+    hbm_frac = BYTES_PER_CELL_UPDATE * value / ws / (peaks.get("hbm_gbs", 6800.0) * 1e9)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_mixed,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD,
+            "n": N,
+            "precision": "mixed (FP32 reconstruction/flux, FP64 accumulation)",
+            "l2": "inputs larger than L2 (state 403 MB per copy)",
+            "parallelism": f"replicas x{ws}",
+        },
+        "fp64": {"value": value64, "ms_per_step": ms_fp64, "steps": steps64,
+                 "roofline": {"bound": "alu", "achieved": achieved64, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": achieved64 / fp64_peak, "traffic": None}},
+        "l1_density_mixed_vs_fp64": l1,
+        "hbm_roofline_frac": hbm_frac,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "face_flux_kernel<float,2,D,true>",
+                     "peak_source": "FP32: SMs x 128 lanes x 2 flop x max SM clock"},
+        "kernel_ms": {name: prof_mixed[k][1] / max(prof_mixed[k][0], 1) for k, name in
+                      ((B.KC_RECON, "cell_poly"), (B.KC_FACE, "face_flux"), (B.KC_UPDATE, "update"), (B.KC_DT, "dt"))},
+        "status": {"mixed": st_mixed, "fp64": st_fp64},
+        "e2e": {"value": ws * e2e_val, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * (args.steps + steps64),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "peaks_source": peak_src,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -156,6 +156,20 @@ int gks_max_wavespeed(gks_handle_t h, double *out);
  * or a negative GKS_ERR_* code if the device work itself failed. */
 int gks_status(gks_handle_t h);
 
+/* Kernel profiler.  While enabled, every kernel the handle launches is
+ * bracketed by CUDA events on the handle's stream; gks_profile_read
+ * synchronises and returns, for one kernel class, the number of launches and
+ * their summed device time in milliseconds since the last reset.  Classes:
+ * GKS_KC_RECON (per-cell reconstruction), GKS_KC_FACE (per-face
+ * reconstruction and gas-kinetic flux), GKS_KC_UPDATE (stage update),
+ * GKS_KC_DT (wave-speed reduction and time step). */
+#define GKS_KC_RECON 0
+#define GKS_KC_FACE 1
+#define GKS_KC_UPDATE 2
+#define GKS_KC_DT 3
+int gks_profile_enable(gks_handle_t h, int on, int reset);
+int gks_profile_read(gks_handle_t h, int kernel_class, long *launches, double *ms);
+
 /* Free everything the handle owns (not a caller workspace).  NULL is a no-op. */
 int gks_destroy(gks_handle_t h);
 
@@ -168,9 +182,13 @@ const char *gks_last_error(gks_handle_t h);
 /* ------------------------------------------------------------------ */
 typedef struct gks_batch_ctx *gks_batch_t;
 
-/* nbatch periodic-or-transmissive 2D grids, grid b with sides nx[b] x ny[b]
- * cells and cell size hs[b].  Every grid keeps its own time step.
- * precision as in gks_opts_t.  opts may be NULL. */
+/* nbatch independent 2D grids (all with boundary condition bc), grid b with
+ * nx[b] x ny[b] cells of size hs[b]; order 4 (Sec. 4.3 on Cartesian cells).
+ * Every grid keeps its own CFL time step.  opts may be NULL; opts->precision
+ * and the scheme constants apply to every grid, opts->stream orders the
+ * batch's work after the caller's (the batch runs on an internal stream that
+ * can be captured); opts->workspace is not supported (GKS_ERR_UNSUPPORTED).
+ * The library allocates one device buffer for all grids. */
 int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs, double gamma, gks_bc_t bc,
                      const gks_opts_t *opts, gks_batch_t *out);
 
@@ -179,10 +197,19 @@ int gks_batch_set_state(gks_batch_t b, int grid, const double *W, const double *
 int gks_batch_get_state(gks_batch_t b, int grid, double *W, double *G, int on_device);
 
 /* nsteps steps of every grid, grid b with dt_b = cfl h_b / (its max |u_d| + c)
- * computed on the device.  The first call records one step into a CUDA graph
- * (tile shapes from the built-in tuning table); later calls replay it.
- * Asynchronous. */
+ * computed on the device.  Per stage three persistent kernels (per-cell
+ * reconstruction, face flux of both directions, update) walk a tile work list
+ * spanning all grids.  The first call times tile-size / block-size candidates
+ * for each kernel (an autotuner; only scratch buffers are written), then
+ * records one step into a CUDA graph; later calls replay the graph (a new cfl
+ * re-records it).  Asynchronous with respect to the host; ordered after the
+ * work already on opts->stream, and later work on that stream waits for it. */
 int gks_batch_run(gks_batch_t b, double cfl, int nsteps);
+
+/* JSON text of the launch shapes the tuner picked (per kernel class: block
+ * size, items per tile, persistent blocks, measured ms); "" before the first
+ * gks_batch_run.  Owned by the handle. */
+const char *gks_batch_tuning(gks_batch_t b);
 
 /* Synchronise and return the status word (as gks_status). */
 int gks_batch_status(gks_batch_t b);

@@ -74,6 +74,8 @@ def lib(build: bool = True):
         "gks_max_wavespeed": (C.c_int, [vp, dp]),
         "gks_status": (C.c_int, [vp]),
         "gks_destroy": (C.c_int, [vp]),
+        "gks_profile_enable": (C.c_int, [vp, C.c_int, C.c_int]),
+        "gks_profile_read": (C.c_int, [vp, C.c_int, C.POINTER(C.c_long), dp]),
         "gks_last_error": (C.c_char_p, [vp]),
         "gks_batch_create": (C.c_int, [C.c_int, ip, ip, dp, C.c_double, C.c_int, op, C.POINTER(vp)]),
         "gks_batch_set_state": (C.c_int, [vp, C.c_int, vp, vp, C.c_int]),
@@ -82,6 +84,7 @@ def lib(build: bool = True):
         "gks_batch_status": (C.c_int, [vp]),
         "gks_batch_destroy": (C.c_int, [vp]),
         "gks_batch_last_error": (C.c_char_p, [vp]),
+        "gks_batch_tuning": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -203,6 +206,20 @@ def gks_status(h) -> int:
     return _check(h, lib().gks_status(h))
 
 
+KC_RECON, KC_FACE, KC_UPDATE, KC_DT = 0, 1, 2, 3
+
+
+def gks_profile_enable(h, on: bool = True, reset: bool = True):
+    return _check(h, lib().gks_profile_enable(h, int(on), int(reset)))
+
+
+def gks_profile_read(h, kernel_class: int):
+    n = C.c_long()
+    ms = C.c_double()
+    _check(h, lib().gks_profile_read(h, kernel_class, C.byref(n), C.byref(ms)))
+    return n.value, ms.value
+
+
 def gks_destroy(h):
     return lib().gks_destroy(h)
 
@@ -210,6 +227,90 @@ def gks_destroy(h):
 def gks_last_error(h) -> str:
     m = lib().gks_last_error(h)
     return m.decode() if m else ""
+
+
+def gks_batch_create(nx, ny, hs, gamma: float, bc: int, opts: Opts | None = None):
+    nb = len(nx)
+    ax = (C.c_int * nb)(*nx)
+    ay = (C.c_int * nb)(*ny)
+    ah = (C.c_double * nb)(*hs)
+    h = C.c_void_p()
+    r = lib().gks_batch_create(nb, ax, ay, ah, gamma, bc, C.byref(opts) if opts is not None else None, C.byref(h))
+    _check(None, r, "gks_batch_last_error")
+    return h
+
+
+def gks_batch_set_state(b, grid: int, W, G):
+    pw, dw = _ptr(W)
+    pg, dg = _ptr(G)
+    if dw != dg:
+        raise ValueError("W and G must both be on the device or both on the host")
+    return _check(b, lib().gks_batch_set_state(b, grid, pw, pg, dw), "gks_batch_last_error")
+
+
+def gks_batch_get_state(b, grid: int, W, G):
+    pw, dw = _ptr(W)
+    pg, dg = _ptr(G)
+    if dw != dg:
+        raise ValueError("W and G must both be on the device or both on the host")
+    return _check(b, lib().gks_batch_get_state(b, grid, pw, pg, dw), "gks_batch_last_error")
+
+
+def gks_batch_run(b, cfl: float, nsteps: int):
+    return _check(b, lib().gks_batch_run(b, float(cfl), int(nsteps)), "gks_batch_last_error")
+
+
+def gks_batch_status(b) -> int:
+    return _check(b, lib().gks_batch_status(b), "gks_batch_last_error")
+
+
+def gks_batch_tuning(b) -> str:
+    m = lib().gks_batch_tuning(b)
+    return m.decode() if m else ""
+
+
+def gks_batch_destroy(b):
+    return lib().gks_batch_destroy(b)
+
+
+class Batch:
+    """Handle wrapper of the batched 2D mode."""
+
+    def __init__(self, nx, ny, hs, gamma=1.4, bc=BC_TRANSMISSIVE, precision=1, stream=None, **consts):
+        o = default_opts()
+        o.precision = precision
+        for k, v in consts.items():
+            setattr(o, k, v)
+        sp = _stream_ptr(stream)
+        o.stream = sp.value if sp is not None else None
+        self.nx, self.ny = list(nx), list(ny)
+        self.h = gks_batch_create(self.nx, self.ny, hs, gamma, bc, o)
+
+    def set_state(self, g, W, G):
+        gks_batch_set_state(self.h, g, W, G)
+
+    def get_state(self, g, W, G):
+        gks_batch_get_state(self.h, g, W, G)
+
+    def run(self, cfl, nsteps):
+        gks_batch_run(self.h, cfl, nsteps)
+
+    def status(self):
+        return gks_batch_status(self.h)
+
+    def tuning(self):
+        return gks_batch_tuning(self.h)
+
+    def close(self):
+        if self.h is not None:
+            gks_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:
@@ -265,6 +366,12 @@ class Solver:
 
     def status(self):
         return gks_status(self.h)
+
+    def profile(self, on=True, reset=True):
+        gks_profile_enable(self.h, on, reset)
+
+    def profile_read(self, kernel_class):
+        return gks_profile_read(self.h, kernel_class)
 
     def close(self):
         if self.h is not None:

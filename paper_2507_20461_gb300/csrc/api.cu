@@ -430,10 +430,48 @@ int gks_status(gks_handle_t c)
     return sync_status(c);
 }
 
+int gks_profile_enable(gks_handle_t c, int on, int reset)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    if (on && !c->prof_ev) {
+        c->prof_ev = new (std::nothrow) cudaEvent_t[2 * gks::kProfCap];
+        c->prof_cls = new (std::nothrow) int[gks::kProfCap];
+        if (!c->prof_ev || !c->prof_cls) return fail(c, GKS_ERR_OOM, "profiler allocation");
+        for (int i = 0; i < 2 * gks::kProfCap; ++i) {
+            cudaError_t e = cudaEventCreate(&c->prof_ev[i]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "profiler events");
+        }
+    }
+    if (c->prof_ev) gks::prof_flush(c);
+    if (reset) {
+        for (int k = 0; k < 8; ++k) {
+            c->prof_launches[k] = 0;
+            c->prof_ms[k] = 0.0;
+        }
+    }
+    c->prof_on = on ? 1 : 0;
+    return GKS_OK;
+}
+
+int gks_profile_read(gks_handle_t c, int cls, long *launches, double *ms)
+{
+    if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
+    if (cls < 0 || cls >= 8) return fail(c, GKS_ERR_ARG, "kernel class out of range");
+    if (c->prof_ev) gks::prof_flush(c);
+    if (launches) *launches = c->prof_launches[cls];
+    if (ms) *ms = c->prof_ms[cls];
+    return GKS_OK;
+}
+
 int gks_destroy(gks_handle_t c)
 {
     if (!c) return GKS_OK;
     cudaStreamSynchronize(c->stream);
+    if (c->prof_ev) {
+        for (int i = 0; i < 2 * gks::kProfCap; ++i) cudaEventDestroy(c->prof_ev[i]);
+        delete[] c->prof_ev;
+        delete[] c->prof_cls;
+    }
     if (c->stage_out) cudaFree(c->stage_out);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;

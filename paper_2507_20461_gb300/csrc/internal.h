@@ -33,10 +33,50 @@ struct gks_ctx {
     /* lazily allocated staging buffer for host-side outputs */
     double *stage_out;
     size_t stage_bytes;
+    /* kernel profiler: event pairs around launches while enabled */
+    int prof_on;
+    int prof_n;
+    cudaEvent_t *prof_ev;  /* 2 * kProfCap events */
+    int *prof_cls;
+    long prof_launches[8];
+    double prof_ms[8];
     char err[256];
 };
 
 namespace gks {
+
+constexpr int kProfCap = 4096;
+
+/* flush recorded event pairs into the per-class totals (synchronises) */
+inline void prof_flush(gks_ctx *c)
+{
+    for (int i = 0; i < c->prof_n; ++i) {
+        float ms = 0.f;
+        cudaEventSynchronize(c->prof_ev[2 * i + 1]);
+        cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]);
+        c->prof_ms[c->prof_cls[i]] += ms;
+        c->prof_launches[c->prof_cls[i]] += 1;
+    }
+    c->prof_n = 0;
+}
+
+/* brackets one kernel launch of class cls with events on the handle's stream */
+struct ProfScope {
+    gks_ctx *c;
+    int slot;
+    ProfScope(gks_ctx *cc, int cls) : c(cc), slot(-1)
+    {
+        if (!c->prof_on) return;
+        if (c->prof_n == kProfCap) prof_flush(c);
+        slot = c->prof_n++;
+        c->prof_cls[slot] = cls;
+        cudaEventRecord(c->prof_ev[2 * slot], c->stream);
+    }
+    ~ProfScope()
+    {
+        if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], c->stream);
+    }
+};
 
 /* per-dimension launchers (k1d.cu, k2d.cu, k3d.cu) */
 template <int M> cudaError_t launch_states(gks_ctx *c, const double *W, const double *G, double *fs_dev);

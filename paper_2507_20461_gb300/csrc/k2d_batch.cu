@@ -1,0 +1,148 @@
+/* Persistent batched kernels of the 2D compact GKS: every block walks the tile
+ * list (grid-stride over tiles), every thread walks the items of its tile.
+ * The per-item arithmetic is the single-grid kernels' (kernels.cuh). */
+#include "batch.h"
+
+namespace gks {
+
+template <typename R>
+__global__ void __launch_bounds__(256) bk_speed(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
+                                                unsigned long long *__restrict__ smax)
+{
+    __shared__ double red[8];
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile T = tiles[ti];
+        const KP &P = gd[T.grid].P;
+        const double *W = gd[T.grid].W;
+        double s = 0.0;
+        for (long c = T.begin + threadIdx.x; c < T.end; c += blockDim.x) {
+            const double rho = W[c];
+            const double u = W[P.ncell + c] / rho, v = W[2 * P.ncell + c] / rho;
+            const double p = (P.gamma - 1.0) * (W[3 * P.ncell + c] - 0.5 * rho * (u * u + v * v));
+            s = fmax(s, fmax(fabs(u), fabs(v)) + sqrt(P.gamma * p / rho));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+            atomicMax(&smax[T.grid], (unsigned long long)__double_as_longlong(isnan(m) ? 1e300 : m));
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void bk_dt(const GridDesc *__restrict__ gd, int nb, double cfl, const unsigned long long *__restrict__ smax,
+                      double *__restrict__ dt)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) dt[b] = cfl * gd[b].P.h / __longlong_as_double((long long)smax[b]);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) bk_poly(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
+                                               int stage)
+{
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile T = tiles[ti];
+        const GridDesc &g = gd[T.grid];
+        const double *W = stage == 1 ? g.W : g.Ws;
+        const double *G = stage == 1 ? g.G : g.Gs;
+        for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x) cell_poly_item<R, 2>(g.P, W, G, (R *)g.B, t);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) bk_flux(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
+                                               int stage, const double *__restrict__ dt, int *__restrict__ status)
+{
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile T = tiles[ti];
+        const GridDesc &g = gd[T.grid];
+        const double *W = stage == 1 ? g.W : g.Ws;
+        const double dtv = dt[T.grid];
+        if (T.kind == 0) {
+            for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x)
+                face_flux_item<R, 2, 0, true>(g.P, W, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
+        } else {
+            for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x)
+                face_flux_item<R, 2, 1, true>(g.P, W, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) bk_update(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
+                                                 int stage, const double *__restrict__ dt, int *__restrict__ status)
+{
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const Tile T = tiles[ti];
+        const GridDesc &g = gd[T.grid];
+        const double dtv = dt[T.grid];
+        for (long c = T.begin + threadIdx.x; c < T.end; c += blockDim.x) {
+            if (stage == 1)
+                update_item<R, 2, 1>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, status, c);
+            else
+                update_item<R, 2, 2>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, status, c);
+        }
+    }
+}
+
+template <typename R> cudaError_t batch_speed(const BatchLaunch &L, const LaunchShape &S, cudaStream_t st)
+{
+    bk_speed<R><<<S.blocks, S.block, 0, st>>>(L.gd, L.tiles, L.ntiles, L.smax);
+    return cudaGetLastError();
+}
+template <typename R> cudaError_t batch_poly(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st)
+{
+    bk_poly<R><<<S.blocks, S.block, 0, st>>>(L.gd, L.tiles, L.ntiles, stage);
+    return cudaGetLastError();
+}
+template <typename R> cudaError_t batch_flux(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st)
+{
+    bk_flux<R><<<S.blocks, S.block, 0, st>>>(L.gd, L.tiles, L.ntiles, stage, L.dt, L.status);
+    return cudaGetLastError();
+}
+template <typename R> cudaError_t batch_update(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st)
+{
+    bk_update<R><<<S.blocks, S.block, 0, st>>>(L.gd, L.tiles, L.ntiles, stage, L.dt, L.status);
+    return cudaGetLastError();
+}
+cudaError_t batch_dt(const GridDesc *gd, int nb, double cfl, const unsigned long long *smax, double *dt, cudaStream_t st)
+{
+    bk_dt<<<(nb + 127) / 128, 128, 0, st>>>(gd, nb, cfl, smax, dt);
+    return cudaGetLastError();
+}
+
+/* resident blocks per SM of one kernel class at a block size */
+int batch_occupancy(int kernel, int precision, int block)
+{
+    int n = 0;
+    switch (kernel) {
+    case BK_SPEED:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_speed<float> : bk_speed<double>, block, 0);
+        break;
+    case BK_POLY:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_poly<float> : bk_poly<double>, block, 0);
+        break;
+    case BK_FLUX:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_flux<float> : bk_flux<double>, block, 0);
+        break;
+    default:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_update<float> : bk_update<double>, block, 0);
+        break;
+    }
+    return n;
+}
+
+#define GKS_BATCH_INST(R)                                                                             \
+    template cudaError_t batch_speed<R>(const BatchLaunch &, const LaunchShape &, cudaStream_t);       \
+    template cudaError_t batch_poly<R>(const BatchLaunch &, const LaunchShape &, int, cudaStream_t);   \
+    template cudaError_t batch_flux<R>(const BatchLaunch &, const LaunchShape &, int, cudaStream_t);   \
+    template cudaError_t batch_update<R>(const BatchLaunch &, const LaunchShape &, int, cudaStream_t);
+GKS_BATCH_INST(float)
+GKS_BATCH_INST(double)
+
+} // namespace gks

@@ -279,12 +279,10 @@ __device__ __forceinline__ bool ext_cell(const KP &P, long t, int &i, int &j, in
 }
 
 template <typename R, int M>
-__global__ void __launch_bounds__(128) cell_poly_kernel(KP P, const double *__restrict__ W, const double *__restrict__ G,
-                                                        R *__restrict__ B)
+__device__ __forceinline__ void cell_poly_item(const KP &P, const double *__restrict__ W, const double *__restrict__ G,
+                                               R *__restrict__ B, long t)
 {
     constexpr int NV = M + 2, NC = Cubic<R, M>::NC, ND = Cubic<R, M>::ND;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= P.next) return;
     int i, j, k;
     if (!ext_cell<M>(P, t, i, j, k)) return;
     /* the seven (five) cells of the cross: own first, then q = 2 e + (side > 0) */
@@ -373,6 +371,14 @@ __global__ void __launch_bounds__(128) cell_poly_kernel(KP P, const double *__re
     }
 }
 
+template <typename R, int M>
+__global__ void __launch_bounds__(128) cell_poly_kernel(KP P, const double *__restrict__ W, const double *__restrict__ G,
+                                                        R *__restrict__ B)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < P.next) cell_poly_item<R, M>(P, W, G, B, t);
+}
+
 template <int M>
 __device__ __forceinline__ long ext_lin(const KP &P, int i, int j, int k)
 {
@@ -386,14 +392,12 @@ __device__ __forceinline__ long ext_lin(const KP &P, int i, int j, int k)
  * face_states[side][v][c][g][face] (double, global axes); FLUX = true the
  * fluxes ff[q][v][g][face] (R, global momentum order). */
 template <typename R, int M, int D, bool FLUX>
-__global__ void __launch_bounds__(128) face_flux_kernel(KP P, const double *__restrict__ W, const R *__restrict__ B,
-                                                        const double *__restrict__ dtp, double *__restrict__ fs,
-                                                        R *__restrict__ ff, int *__restrict__ status)
+__device__ __forceinline__ void face_flux_item(const KP &P, const double *__restrict__ W, const R *__restrict__ B,
+                                               double dtv, double *__restrict__ fs, R *__restrict__ ff,
+                                               int *__restrict__ status, long t)
 {
     constexpr int NV = M + 2, NC = Cubic<R, M>::NC, NG = (M == 2) ? 2 : 4;
     const long nf = P.nface[D];
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nf * NG) return;
     const int g = (int)(t / nf);
     const long fl = t - (long)g * nf;
     int e0 = P.n[0] + (D == 0), e1 = P.n[1] + (D == 1);
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(128) face_flux_kernel(KP P, const double *__re
         }
     }
     R F[NV], Ft[NV], Wh[NV];
-    const R dt = R(dtp[0]);
+    const R dt = R(dtv);
     if (!gks_point<R, M>(P.fp, dt, Wl, Wr, dWl, dWr, F, Ft, Wh)) {
         atomicOr(status, ST_FLUX);
 #pragma unroll
@@ -490,6 +494,16 @@ __global__ void __launch_bounds__(128) face_flux_kernel(KP P, const double *__re
     }
 }
 
+template <typename R, int M, int D, bool FLUX>
+__global__ void __launch_bounds__(128) face_flux_kernel(KP P, const double *__restrict__ W, const R *__restrict__ B,
+                                                        const double *__restrict__ dtp, double *__restrict__ fs,
+                                                        R *__restrict__ ff, int *__restrict__ status)
+{
+    constexpr int NG = (M == 2) ? 2 : 4;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < P.nface[D] * NG) face_flux_item<R, M, D, FLUX>(P, W, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
+}
+
 /* ------------------------------------------------------------------ */
 /* FP64 stage update                                                   */
 /* ------------------------------------------------------------------ */
@@ -506,18 +520,15 @@ __device__ __forceinline__ long face_of(const KP &P, int d, int i, int j, int k,
  * STAGE 2: W += Acc - dt^2/3 L(Ft*),        G  = Gauss(W*(dt/2))
  * with L(q)_j = (1/h) sum_d sum_g w_g (q(+d face) - q(-d face)). */
 template <typename R, int M, int STAGE>
-__global__ void __launch_bounds__(256) update_kernel(KP P, const R *__restrict__ ff, const double *__restrict__ dtp,
-                                                    double *__restrict__ W, double *__restrict__ G,
-                                                    double *__restrict__ Ws, double *__restrict__ Gs,
-                                                    double *__restrict__ Acc, int *__restrict__ status)
+__device__ __forceinline__ void update_item(const KP &P, const R *__restrict__ ff, double dt, double *__restrict__ W,
+                                            double *__restrict__ G, double *__restrict__ Ws, double *__restrict__ Gs,
+                                            double *__restrict__ Acc, int *__restrict__ status, long cell)
 {
     constexpr int NV = M + 2, NG = (M == 1) ? 1 : ((M == 2) ? 2 : 4);
-    const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= P.ncell) return;
     const int i = (int)(cell % P.n[0]);
     const int j = (M >= 2) ? (int)((cell / P.n[0]) % P.n[1]) : 0;
     const int k = (M >= 3) ? (int)(cell / ((long)P.n[0] * P.n[1])) : 0;
-    const double dt = dtp[0], ih = P.ih, wg = 1.0 / NG;
+    const double ih = P.ih, wg = 1.0 / NG;
     const long nft = P.nftot;
     long fp[M], fm[M];
 #pragma unroll
@@ -564,6 +575,16 @@ __global__ void __launch_bounds__(256) update_kernel(KP P, const R *__restrict__
     if (!(p > 0.0)) st |= ST_P;
     if (!isfinite(p) || !isfinite(Wn[0])) st |= ST_NAN;
     if (st) atomicOr(status, st);
+}
+
+template <typename R, int M, int STAGE>
+__global__ void __launch_bounds__(256) update_kernel(KP P, const R *__restrict__ ff, const double *__restrict__ dtp,
+                                                    double *__restrict__ W, double *__restrict__ G,
+                                                    double *__restrict__ Ws, double *__restrict__ Gs,
+                                                    double *__restrict__ Acc, int *__restrict__ status)
+{
+    const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell < P.ncell) update_item<R, M, STAGE>(P, ff, dtp[0], W, G, Ws, Gs, Acc, status, cell);
 }
 
 /* ------------------------------------------------------------------ */

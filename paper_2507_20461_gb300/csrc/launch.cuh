@@ -12,14 +12,19 @@ static cudaError_t flux_impl(gks_ctx *c, const double *W, const double *G, doubl
     R *ff = (R *)c->ff;
     if constexpr (M == 1) {
         const unsigned nb = blocks_for(P.n[0] + 1);
+        ProfScope ps(c, GKS_KC_FACE);
         if (flux) face1d_kernel<R, true><<<nb, kBlock, 0, c->stream>>>(P, W, G, c->dt, nullptr, ff, c->status);
         else face1d_kernel<R, false><<<nb, kBlock, 0, c->stream>>>(P, W, G, c->dt, fs_dev, nullptr, c->status);
     } else {
         constexpr int NG = (M == 2) ? 2 : 4;
         R *B = (R *)c->B;
-        cell_poly_kernel<R, M><<<blocks_for(P.next), kBlock, 0, c->stream>>>(P, W, G, B);
+        {
+            ProfScope ps(c, GKS_KC_RECON);
+            cell_poly_kernel<R, M><<<blocks_for(P.next), kBlock, 0, c->stream>>>(P, W, G, B);
+        }
         for (int d = 0; d < M; ++d) {
             const unsigned nb = blocks_for(P.nface[d] * NG);
+            ProfScope ps(c, GKS_KC_FACE);
 #define GKS_FACE(D)                                                                                           \
     if (d == D) {                                                                                             \
         if (flux) face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, W, B, c->dt, nullptr, ff, c->status); \
@@ -49,6 +54,7 @@ template <typename R, int M> static cudaError_t update_impl(gks_ctx *c, int stag
     const KP &P = c->kp;
     const unsigned nb = blocks_for(P.ncell, 256);
     const R *ff = (const R *)c->ff;
+    ProfScope ps(c, GKS_KC_UPDATE);
     if (stage == 1)
         update_kernel<R, M, 1><<<nb, 256, 0, c->stream>>>(P, ff, c->dt, c->W, c->G, c->Ws, c->Gs, c->Acc, c->status);
     else
@@ -71,6 +77,7 @@ template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl)
     long want = (c->kp.ncell + 255) / 256;
     long cap = (long)nsm * 8;
     const unsigned nb = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+    ProfScope ps(c, GKS_KC_DT);
     wavespeed_kernel<M><<<nb, 256, 0, c->stream>>>(c->kp, c->W, c->smax);
     if (cfl > 0.0) dt_from_speed_kernel<<<1, 1, 0, c->stream>>>(c->smax, cfl * c->h, c->dt);
     return cudaGetLastError();

@@ -1,0 +1,117 @@
+"""Batched 2D mode (many independent uneven grids, persistent kernels over a
+tile work list, one step recorded in a CUDA graph) against the single-grid
+path and the oracle, on cuda:0, through the C ABI."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2507_20461_gb300 import binding as B
+from paper_2507_20461_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+SIZES = [(16, 20), (33, 17), (64, 64), (8, 40), (50, 31), (2, 3)]
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def _ics(sizes, base_seed):
+    out = []
+    for g, (nx, ny) in enumerate(sizes):
+        W, G, h = I.quadrants_2d(ny, seed=base_seed + g, nx=nx)
+        out.append((W, G, h))
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_single_grid(precision):
+    ics = _ics(SIZES, 700)
+    nx = [s[0] for s in SIZES]
+    ny = [s[1] for s in SIZES]
+    hs = [ic[2] for ic in ics]
+    bt = B.Batch(nx, ny, hs, bc=B.BC_TRANSMISSIVE, precision=precision)
+    for g, (W, G, h) in enumerate(ics):
+        bt.set_state(g, _dev(W), _dev(G))
+    bt.run(0.4, 6)
+    assert bt.status() == 0
+    assert '"flux"' in bt.tuning()
+    bt.run(0.4, 4)  # graph replay after the first recording
+    for g, (W, G, h) in enumerate(ics):
+        Wb, Gb = _dev(W), _dev(G)
+        bt.get_state(g, Wb, Gb)
+        s = B.Solver((nx[g], ny[g]), lo=[0, 0], hi=[nx[g] * h, ny[g] * h], bc=B.BC_TRANSMISSIVE, precision=precision)
+        Ws, Gs = _dev(W), _dev(G)
+        s.set_state(Ws, Gs)
+        s.step_cfl(0.4, 10)
+        s.get_state(Ws, Gs)
+        s.close()
+        np.testing.assert_allclose(Wb.cpu().numpy(), Ws.cpu().numpy(), rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(Gb.cpu().numpy(), Gs.cpu().numpy(), rtol=1e-10, atol=1e-9)
+    bt.close()
+
+
+def test_batch_fp64_matches_oracle():
+    sizes = [(24, 18), (13, 29)]
+    ics = _ics(sizes, 900)
+    bt = B.Batch([s[0] for s in sizes], [s[1] for s in sizes], [ic[2] for ic in ics], bc=B.BC_TRANSMISSIVE, precision=0)
+    for g, (W, G, h) in enumerate(ics):
+        bt.set_state(g, _dev(W), _dev(G))
+    bt.run(0.4, 3)
+    for g, (W, G, h) in enumerate(ics):
+        cfg = O.make_cfg(2, sizes[g], h, bc=1)
+        Wo, Go = W.copy(), G.copy()
+        for _ in range(3):
+            dt = 0.4 * h / O.max_wavespeed(cfg, Wo)
+            assert O.step(cfg, dt, Wo, Go) == 0
+        Wb, Gb = _dev(W), _dev(G)
+        bt.get_state(g, Wb, Gb)
+        Wg = Wb.cpu().numpy()
+        rel = np.abs(Wg - Wo).sum(axis=(1, 2)) / np.abs(Wo).sum(axis=(1, 2))
+        assert rel.max() <= 1e-12, rel
+    bt.close()
+
+
+def test_config4_full_batch():
+    """256 grids, sides log-uniform in [64, 1024], four-quadrant ICs (seed base + i),
+    mixed precision: 30 steps stay admissible; sampled one-step windows of
+    three grids agree with the FP64 oracle to mixed-precision accuracy."""
+    nb = 256
+    sides = I.batch_sizes(nb, seed=20464)
+    hs = [1.0 / n for n in sides]
+    bt = B.Batch(sides, sides, hs, bc=B.BC_TRANSMISSIVE, precision=1)
+    ics = []
+    for g, n in enumerate(sides):
+        W, G, h = I.quadrants_2d(n, seed=20464 + g)
+        bt.set_state(g, _dev(W), _dev(G))
+        if g < 3:
+            ics.append((W, G, h))
+    bt.run(0.4, 1)
+    assert bt.status() == 0
+    for g, (W, G, h) in enumerate(ics):
+        n = sides[g]
+        Wb, Gb = _dev(W), _dev(G)
+        bt.get_state(g, Wb, Gb)
+        Wn = Wb.cpu().numpy()
+        cfg_full = O.make_cfg(2, (n, n), h, bc=1)
+        dt = 0.4 * h / O.max_wavespeed(cfg_full, W)
+        c = n // 2
+        idx = np.arange(c - 8, c + 9)
+        sl = np.ix_(idx, idx)
+        Ww = np.ascontiguousarray(W[(slice(None),) + sl])
+        Gw = np.ascontiguousarray(G[(slice(None), slice(None)) + sl])
+        assert O.step(O.make_cfg(2, (17, 17), h, bc=1), dt, Ww, Gw) == 0
+        np.testing.assert_allclose(Wn[:, c, c], Ww[:, 8, 8], rtol=2e-5, atol=2e-5)
+    bt.run(0.4, 29)
+    assert bt.status() == 0
+    bt.close()
+
+
+def test_batch_rejects_bad_sizes():
+    with pytest.raises(B.GksError) as e:
+        B.Batch([8, 0], [8, 8], [0.1, 0.1])
+    assert e.value.code == B.ERR_ARG
