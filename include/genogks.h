@@ -178,6 +178,41 @@ int gks_destroy(gks_handle_t h);
 const char *gks_last_error(gks_handle_t h);
 
 /* ------------------------------------------------------------------ */
+/* Flux without allocation                                              */
+/* ------------------------------------------------------------------ */
+/* The paper has no counterpart of this entry point; it serves callers that
+ * cannot allocate device memory (code running where cudaMalloc is not
+ * available or not allowed, such as a plugin or callback that must not own
+ * memory, a process whose device allocator belongs to another framework, or
+ * a latency-critical loop that cannot afford an allocation's implicit
+ * synchronisation).
+ *
+ * Same result as gks_flux on a 2D FP64 grid of nx x ny cells of size h:
+ * face_flux[q][v][g][face] (3 * 4 * 2 * F doubles), from the state W
+ * (4 x nx x ny) and G (2 x 4 x nx x ny) doubles.  W, G and face_flux are
+ * caller-owned DEVICE memory of the current device; the work is enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) and the call
+ * synchronises that stream before it returns.  opts may be NULL (defaults);
+ * opts->precision must be 0 and opts->stream / workspace are ignored.
+ *
+ * It allocates nothing: the only scratch it needs lives in one static device
+ * array of 4,147,456 bytes (about 4 MiB) that every GPU which loads the
+ * library holds until the process exits, which limits the grid to
+ * (nx + 2) * (ny + 2) <= 14400 cells including the one-cell ghost ring (for
+ * example 118 x 118); larger grids return
+ * GKS_ERR_ARG, as do invalid sizes, gamma, bc, dt or NULL pointers.
+ * GKS_ERR_UNSUPPORTED: precision != 0.  GKS_ERR_NONPHYSICAL: a face state the
+ * flux could not use.  GKS_ERR_CUDA: a CUDA call failed.
+ *
+ * The first call on a device looks up the device address of that array
+ * (with the device current); make that first call before any stream capture.
+ * Every call on a device shares the array and leaves its contents behind;
+ * calls that overlap on the GPU (other streams or unordered host threads)
+ * race on it and must be serialised by the caller. */
+int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc_t bc, const gks_opts_t *opts, const double *W,
+                       const double *G, double dt, double *face_flux, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Batched mode: many independent 2D grids of uneven sizes              */
 /* ------------------------------------------------------------------ */
 typedef struct gks_batch_ctx *gks_batch_t;
