@@ -30,8 +30,9 @@ int cuda_fail(gks_ctx *c, cudaError_t e, const char *where)
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t W, G, Ws, Gs, Acc, small, B, ff, total;
+    size_t W, G, Ws, Gs, Acc, small, B, ff, sh0, sh1, total;
     size_t B_elems, ff_elems;
+    int shadows;
 };
 
 bool grid_ok(const gks_grid_t *g, double *h)
@@ -85,6 +86,11 @@ Layout layout(const gks_grid_t *g, int precision)
     L.small = off; off = align_up(off + 256);
     L.B = off; off = align_up(off + rs * L.B_elems);
     L.ff = off; off = align_up(off + rs * L.ff_elems);
+    /* FP32 shadows (mixed precision, 2D/3D): hi, lo (nv x cells), g (m x nv x cells) */
+    L.shadows = (precision == 1 && m >= 2);
+    const size_t shb = L.shadows ? sizeof(float) * (size_t)(2 + m) * nv * ncell : 0;
+    L.sh0 = off; off = align_up(off + shb);
+    L.sh1 = off; off = align_up(off + shb);
     L.total = off;
     return L;
 }
@@ -117,12 +123,21 @@ __global__ void widen_kernel(const float *__restrict__ in, double *__restrict__ 
         out[i] = (double)in[i];
 }
 
-cudaError_t run_flux(gks_ctx *c, const double *W, const double *G)
+cudaError_t run_flux(gks_ctx *c, int input)
 {
     switch (c->dim) {
-    case 1: return gks::launch_flux<1>(c, W, G);
-    case 2: return gks::launch_flux<2>(c, W, G);
-    default: return gks::launch_flux<3>(c, W, G);
+    case 1: return gks::launch_flux<1>(c, input);
+    case 2: return gks::launch_flux<2>(c, input);
+    default: return gks::launch_flux<3>(c, input);
+    }
+}
+
+cudaError_t run_shadow(gks_ctx *c)
+{
+    switch (c->dim) {
+    case 1: return gks::launch_shadow<1>(c);
+    case 2: return gks::launch_shadow<2>(c);
+    default: return gks::launch_shadow<3>(c);
     }
 }
 
@@ -148,9 +163,9 @@ cudaError_t run_wavespeed(gks_ctx *c, double cfl)
 int two_stages(gks_ctx *c)
 {
     cudaError_t e;
-    if ((e = run_flux(c, c->W, c->G)) != cudaSuccess) return cuda_fail(c, e, "stage 1 flux");
+    if ((e = run_flux(c, 0)) != cudaSuccess) return cuda_fail(c, e, "stage 1 flux");
     if ((e = run_update(c, 1)) != cudaSuccess) return cuda_fail(c, e, "stage 1 update");
-    if ((e = run_flux(c, c->Ws, c->Gs)) != cudaSuccess) return cuda_fail(c, e, "stage 2 flux");
+    if ((e = run_flux(c, 1)) != cudaSuccess) return cuda_fail(c, e, "stage 2 flux");
     if ((e = run_update(c, 2)) != cudaSuccess) return cuda_fail(c, e, "stage 2 update");
     return GKS_OK;
 }
@@ -248,6 +263,15 @@ int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc
     c->status = (int *)(base + L.small + 128);
     c->B = base + L.B;
     c->ff = base + L.ff;
+    c->shadows = L.shadows;
+    if (L.shadows) {
+        const size_t nvc = (size_t)c->nv;
+        long nc = 1;
+        for (int a = 0; a < grid->dim; ++a) nc *= grid->n[a];
+        float *s0 = (float *)(base + L.sh0), *s1 = (float *)(base + L.sh1);
+        c->s0 = gks::Shadow{s0, s0 + nvc * nc, s0 + 2 * nvc * nc};
+        c->s1 = gks::Shadow{s1, s1 + nvc * nc, s1 + 2 * nvc * nc};
+    }
     c->B_elems = L.B_elems;
     c->ff_elems = L.ff_elems;
 
@@ -305,6 +329,7 @@ int gks_set_state(gks_handle_t c, const double *W, const double *G, int on_devic
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = cudaMemcpyAsync(c->W, W, nW * sizeof(double), k, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->G, G, nG * sizeof(double), k, c->stream);
+    if (e == cudaSuccess) e = run_shadow(c);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
@@ -340,9 +365,9 @@ int geno_reconstruct(gks_handle_t c, double *fs, int on_device)
     }
     cudaError_t e;
     switch (c->dim) {
-    case 1: e = gks::launch_states<1>(c, c->W, c->G, dst); break;
-    case 2: e = gks::launch_states<2>(c, c->W, c->G, dst); break;
-    default: e = gks::launch_states<3>(c, c->W, c->G, dst); break;
+    case 1: e = gks::launch_states<1>(c, 0, dst); break;
+    case 2: e = gks::launch_states<2>(c, 0, dst); break;
+    default: e = gks::launch_states<3>(c, 0, dst); break;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "reconstruct");
     if (!on_device) {
@@ -359,7 +384,7 @@ int gks_flux(gks_handle_t c, double dt, double *out, int on_device)
     if (!out) return fail(c, GKS_ERR_ARG, "face_flux is NULL");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GKS_ERR_ARG, "dt must be finite and > 0");
     gks::set_scalar_kernel<<<1, 1, 0, c->stream>>>(c->dt, dt);
-    cudaError_t e = run_flux(c, c->W, c->G);
+    cudaError_t e = run_flux(c, 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "flux");
     const size_t n = c->ff_elems;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

@@ -285,6 +285,7 @@ int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs,
         base[g] = off;
         off += al(sizeof(double) * 4 * P.ncell) * 3 + al(sizeof(double) * 8 * P.ncell) * 2 + al(rs * 4 * GENO_NC2 * P.next) +
                al(rs * 3 * 4 * 2 * P.nftot);
+        if (o.precision == 1) off += 2 * al(sizeof(float) * 16 * P.ncell); /* shadows: hi, lo, g */
     }
     b->ws_bytes = off;
     e = cudaMalloc(&b->ws, off);
@@ -308,7 +309,13 @@ int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs,
         D.G = (double *)(w + o2); o2 += al(sizeof(double) * 8 * P.ncell);
         D.Gs = (double *)(w + o2); o2 += al(sizeof(double) * 8 * P.ncell);
         D.B = w + o2; o2 += al(rs * 4 * GENO_NC2 * P.next);
-        D.ff = w + o2;
+        D.ff = w + o2; o2 += al(rs * 3 * 4 * 2 * P.nftot);
+        D.s0 = D.s1 = gks::Shadow{nullptr, nullptr, nullptr};
+        if (o.precision == 1) {
+            float *a = (float *)(w + o2), *c2 = (float *)(w + o2 + al(sizeof(float) * 16 * P.ncell));
+            D.s0 = gks::Shadow{a, a + 4 * P.ncell, a + 8 * P.ncell};
+            D.s1 = gks::Shadow{c2, c2 + 4 * P.ncell, c2 + 8 * P.ncell};
+        }
     }
     e = cudaMalloc(&b->dd, sizeof(GridDesc) * nbatch);
     if (e == cudaSuccess) e = cudaMemcpy(b->dd, b->hd.data(), sizeof(GridDesc) * nbatch, cudaMemcpyHostToDevice);
@@ -339,8 +346,12 @@ int gks_batch_set_state(gks_batch_t b, int grid, const double *W, const double *
     const GridDesc &D = b->hd[grid];
     const size_t n = (size_t)4 * D.P.ncell;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    cudaError_t e = cudaMemcpyAsync(D.W, W, n * sizeof(double), k, b->stream);
+    /* the caller's buffers may still be written by work on its stream */
+    cudaError_t e = cudaEventRecord(b->ev_in, b->user_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_in, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D.W, W, n * sizeof(double), k, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.G, G, 2 * n * sizeof(double), k, b->stream);
+    if (e == cudaSuccess && b->precision == 1) e = gks::batch_shadow(D, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     return e == cudaSuccess ? GKS_OK : bcuda(b, e, "batch set_state");
@@ -353,8 +364,10 @@ int gks_batch_get_state(gks_batch_t b, int grid, double *W, double *G, int on_de
     const GridDesc &D = b->hd[grid];
     const size_t n = (size_t)4 * D.P.ncell;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    cudaError_t e = cudaSuccess;
-    if (W) e = cudaMemcpyAsync(W, D.W, n * sizeof(double), k, b->stream);
+    /* the caller's stream may still use the destination buffers */
+    cudaError_t e = cudaEventRecord(b->ev_in, b->user_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_in, 0);
+    if (e == cudaSuccess && W) e = cudaMemcpyAsync(W, D.W, n * sizeof(double), k, b->stream);
     if (e == cudaSuccess && G) e = cudaMemcpyAsync(G, D.G, 2 * n * sizeof(double), k, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "batch get_state");

@@ -11,6 +11,7 @@ struct GridDesc {
     KP P;
     double *W, *G, *Ws, *Gs, *Acc;
     void *B, *ff;
+    Shadow s0, s1; /* FP32 shadows (mixed precision only) */
 };
 
 /* a contiguous range [begin, end) of one kernel's index space on one grid;
@@ -43,6 +44,7 @@ template <typename R> cudaError_t batch_poly(const BatchLaunch &L, const LaunchS
 template <typename R> cudaError_t batch_flux(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st);
 template <typename R> cudaError_t batch_update(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st);
 cudaError_t batch_dt(const GridDesc *gd, int nb, double cfl, const unsigned long long *smax, double *dt, cudaStream_t st);
+cudaError_t batch_shadow(const GridDesc &g, cudaStream_t st);
 int batch_occupancy(int kernel, int precision, int block);
 
 } // namespace gks

@@ -17,6 +17,10 @@ struct gks_ctx {
     cudaStream_t stream;
     /* state and stage buffers (FP64) */
     double *W, *G, *Ws, *Gs, *Acc;
+    /* mixed precision, 2D/3D: FP32 shadows of the step's input state (s0) and
+     * of the stage-1 output (s1) that the reconstruction and flux read */
+    gks::Shadow s0, s1;
+    int shadows;
     /* device scalars */
     double *dt;
     unsigned long long *smax;
@@ -79,10 +83,12 @@ struct ProfScope {
 };
 
 /* per-dimension launchers (k1d.cu, k2d.cu, k3d.cu) */
-template <int M> cudaError_t launch_states(gks_ctx *c, const double *W, const double *G, double *fs_dev);
-template <int M> cudaError_t launch_flux(gks_ctx *c, const double *W, const double *G);
+/* input: 0 = the step's input state (W, G), 1 = the stage-1 output (W*, G*) */
+template <int M> cudaError_t launch_states(gks_ctx *c, int input, double *fs_dev);
+template <int M> cudaError_t launch_flux(gks_ctx *c, int input);
 template <int M> cudaError_t launch_update(gks_ctx *c, int stage);
 template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl);
+template <int M> cudaError_t launch_shadow(gks_ctx *c);
 
 inline int ngauss(int m) { return m == 1 ? 1 : (m == 2 ? 2 : 4); }
 inline int ncubic(int m) { return m == 2 ? GENO_NC2 : (m == 3 ? GENO_NC3 : 0); }

@@ -5,6 +5,17 @@
 
 namespace gks {
 
+template <typename R> __device__ __forceinline__ Src<R> stage_src_of(const GridDesc &g, int stage);
+template <> __device__ __forceinline__ Src<double> stage_src_of<double>(const GridDesc &g, int stage)
+{
+    return stage == 1 ? Src<double>{g.W, g.G} : Src<double>{g.Ws, g.Gs};
+}
+template <> __device__ __forceinline__ Src<float> stage_src_of<float>(const GridDesc &g, int stage)
+{
+    const Shadow &s = stage == 1 ? g.s0 : g.s1;
+    return Src<float>{s.hi, s.lo, s.g};
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) bk_speed(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
                                                 unsigned long long *__restrict__ smax)
@@ -13,14 +24,19 @@ __global__ void __launch_bounds__(256) bk_speed(const GridDesc *__restrict__ gd,
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile T = tiles[ti];
         const KP &P = gd[T.grid].P;
-        const double *W = gd[T.grid].W;
-        double s = 0.0;
+        /* the FP64 state, or its FP32 shadow in mixed precision */
+        const R *W;
+        if constexpr (sizeof(R) == sizeof(float)) W = gd[T.grid].s0.hi;
+        else W = gd[T.grid].W;
+        const R gam = R(P.gamma);
+        R sr = R(0);
         for (long c = T.begin + threadIdx.x; c < T.end; c += blockDim.x) {
-            const double rho = W[c];
-            const double u = W[P.ncell + c] / rho, v = W[2 * P.ncell + c] / rho;
-            const double p = (P.gamma - 1.0) * (W[3 * P.ncell + c] - 0.5 * rho * (u * u + v * v));
-            s = fmax(s, fmax(fabs(u), fabs(v)) + sqrt(P.gamma * p / rho));
+            const R rho = W[c];
+            const R u = W[P.ncell + c] / rho, v = W[2 * P.ncell + c] / rho;
+            const R p = (gam - R(1)) * (W[3 * P.ncell + c] - R(0.5) * rho * (u * u + v * v));
+            sr = fmax(sr, fmax(fabs(u), fabs(v)) + sqrt(gam * p / rho));
         }
+        double s = (double)sr;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -48,9 +64,8 @@ __global__ void __launch_bounds__(128) bk_poly(const GridDesc *__restrict__ gd, 
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile T = tiles[ti];
         const GridDesc &g = gd[T.grid];
-        const double *W = stage == 1 ? g.W : g.Ws;
-        const double *G = stage == 1 ? g.G : g.Gs;
-        for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x) cell_poly_item<R, 2>(g.P, W, G, (R *)g.B, t);
+        const Src<R> src = stage_src_of<R>(g, stage);
+        for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x) cell_poly_item<R, 2>(g.P, src, (R *)g.B, t);
     }
 }
 
@@ -61,14 +76,14 @@ __global__ void __launch_bounds__(128) bk_flux(const GridDesc *__restrict__ gd, 
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile T = tiles[ti];
         const GridDesc &g = gd[T.grid];
-        const double *W = stage == 1 ? g.W : g.Ws;
+        const Src<R> src = stage_src_of<R>(g, stage);
         const double dtv = dt[T.grid];
         if (T.kind == 0) {
             for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x)
-                face_flux_item<R, 2, 0, true>(g.P, W, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
+                face_flux_item<R, 2, 0, true>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
         } else {
             for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x)
-                face_flux_item<R, 2, 1, true>(g.P, W, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
+                face_flux_item<R, 2, 1, true>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
         }
     }
 }
@@ -83,9 +98,9 @@ __global__ void __launch_bounds__(256) bk_update(const GridDesc *__restrict__ gd
         const double dtv = dt[T.grid];
         for (long c = T.begin + threadIdx.x; c < T.end; c += blockDim.x) {
             if (stage == 1)
-                update_item<R, 2, 1>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, status, c);
+                update_item<R, 2, 1>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status, c);
             else
-                update_item<R, 2, 2>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, status, c);
+                update_item<R, 2, 2>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status, c);
         }
     }
 }
@@ -110,6 +125,13 @@ template <typename R> cudaError_t batch_update(const BatchLaunch &L, const Launc
     bk_update<R><<<S.blocks, S.block, 0, st>>>(L.gd, L.tiles, L.ntiles, stage, L.dt, L.status);
     return cudaGetLastError();
 }
+cudaError_t batch_shadow(const GridDesc &g, cudaStream_t st)
+{
+    const long want = (g.P.ncell + 255) / 256;
+    shadow_kernel<2><<<(unsigned)(want < 4096 ? (want > 0 ? want : 1) : 4096), 256, 0, st>>>(g.P, g.W, g.G, g.s0);
+    return cudaGetLastError();
+}
+
 cudaError_t batch_dt(const GridDesc *gd, int nb, double cfl, const unsigned long long *smax, double *dt, cudaStream_t st)
 {
     bk_dt<<<(nb + 127) / 128, 128, 0, st>>>(gd, nb, cfl, smax, dt);

@@ -44,6 +44,37 @@ struct KP {
     FluxParams fp;
 };
 
+/* FP32 shadow of a state (mixed precision, 2D/3D): hi = float(W),
+ * lo = float(W - hi) (so neighbour differences keep FP64-level accuracy),
+ * g = float(grad W).  hi/lo: nv x cells, g: M x nv x cells. */
+struct Shadow {
+    float *hi, *lo, *g;
+};
+
+/* What the reconstruction and flux kernels read of a stage's input state:
+ * the FP64 arrays (R = double) or the FP32 shadow (R = float).  Indices:
+ * v * ncell + cell for averages, (a * nv + v) * ncell + cell for gradients. */
+template <typename R> struct Src;
+template <> struct Src<double> {
+    const double *W, *G;
+    __device__ __forceinline__ double w0(long i) const { return W[i]; }
+    __device__ __forceinline__ double delta(long iq, long i0) const { return W[iq] - W[i0]; }
+    __device__ __forceinline__ double grad(long i) const { return G[i]; }
+};
+template <> struct Src<float> {
+    const float *hi, *lo, *g;
+    __device__ __forceinline__ float w0(long i) const { return hi[i]; }
+    __device__ __forceinline__ float delta(long iq, long i0) const { return (hi[iq] - hi[i0]) + (lo[iq] - lo[i0]); }
+    __device__ __forceinline__ float grad(long i) const { return g[i]; }
+};
+
+__device__ __forceinline__ void split_store(double w, float *hi, float *lo, long i)
+{
+    const float a = (float)w;
+    hi[i] = a;
+    lo[i] = (float)(w - (double)a);
+}
+
 __device__ __forceinline__ int map_idx(int i, int n, int bc, int &flip)
 {
     if (i >= 0 && i < n) return i;
@@ -279,8 +310,7 @@ __device__ __forceinline__ bool ext_cell(const KP &P, long t, int &i, int &j, in
 }
 
 template <typename R, int M>
-__device__ __forceinline__ void cell_poly_item(const KP &P, const double *__restrict__ W, const double *__restrict__ G,
-                                               R *__restrict__ B, long t)
+__device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R *__restrict__ B, long t)
 {
     constexpr int NV = M + 2, NC = Cubic<R, M>::NC, ND = Cubic<R, M>::ND;
     int i, j, k;
@@ -298,21 +328,21 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const double *__rest
     const double h = P.h;
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) {
-        const double W0 = W[v * P.ncell + cl[0]];
         R d[ND];
+        const R hr = R(h);
 #pragma unroll
         for (int q = 0; q < 2 * M; ++q) {
-            d[q * (1 + M)] = R(W[v * P.ncell + cl[1 + q]] - W0);
+            d[q * (1 + M)] = R(src.delta(v * P.ncell + cl[1 + q], v * P.ncell + cl[0]));
 #pragma unroll
             for (int a = 0; a < M; ++a) {
-                const double g = G[(a * NV + v) * P.ncell + cl[1 + q]] * h;
-                d[q * (1 + M) + 1 + a] = R(fl[1 + q][a] ? -g : g);
+                const R g = src.grad((a * NV + v) * P.ncell + cl[1 + q]) * hr;
+                d[q * (1 + M) + 1 + a] = fl[1 + q][a] ? -g : g;
             }
         }
 #pragma unroll
         for (int a = 0; a < M; ++a) {
-            const double g = G[(a * NV + v) * P.ncell + cl[0]] * h;
-            d[2 * M * (1 + M) + a] = R(fl[0][a] ? -g : g);
+            const R g = src.grad((a * NV + v) * P.ncell + cl[0]) * hr;
+            d[2 * M * (1 + M) + a] = fl[0][a] ? -g : g;
         }
         R c[NC];
         Cubic<R, M>::fit(d, c);
@@ -372,11 +402,10 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const double *__rest
 }
 
 template <typename R, int M>
-__global__ void __launch_bounds__(128) cell_poly_kernel(KP P, const double *__restrict__ W, const double *__restrict__ G,
-                                                        R *__restrict__ B)
+__global__ void __launch_bounds__(128) cell_poly_kernel(KP P, Src<R> src, R *__restrict__ B)
 {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < P.next) cell_poly_item<R, M>(P, W, G, B, t);
+    if (t < P.next) cell_poly_item<R, M>(P, src, B, t);
 }
 
 template <int M>
@@ -392,9 +421,9 @@ __device__ __forceinline__ long ext_lin(const KP &P, int i, int j, int k)
  * face_states[side][v][c][g][face] (double, global axes); FLUX = true the
  * fluxes ff[q][v][g][face] (R, global momentum order). */
 template <typename R, int M, int D, bool FLUX>
-__device__ __forceinline__ void face_flux_item(const KP &P, const double *__restrict__ W, const R *__restrict__ B,
-                                               double dtv, double *__restrict__ fs, R *__restrict__ ff,
-                                               int *__restrict__ status, long t)
+__device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, const R *__restrict__ B, double dtv,
+                                               double *__restrict__ fs, R *__restrict__ ff, int *__restrict__ status,
+                                               long t)
 {
     constexpr int NV = M + 2, NC = Cubic<R, M>::NC, NG = (M == 2) ? 2 : 4;
     const long nf = P.nface[D];
@@ -422,9 +451,9 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const double *__rest
             for (int kk = 0; kk < NC; ++kk) c[kk] = B[((long)v * NC + kk) * P.next + ce];
             if (side == 0) CubicEval<R, M, D, 1>::run(g, c, out);
             else CubicEval<R, M, D, 0>::run(g, c, out);
-            const double w0 = W[v * P.ncell + cl];
-            cw[side][v] = R(w0);
-            st[side][v][0] = R(w0) + out[0];
+            const R w0 = R(src.w0(v * P.ncell + cl));
+            cw[side][v] = w0;
+            st[side][v][0] = w0 + out[0];
 #pragma unroll
             for (int a = 0; a < M; ++a) st[side][v][1 + a] = out[1 + a] * R(P.ih);
         }
@@ -494,14 +523,17 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const double *__rest
     }
 }
 
+/* 128 threads; the FP32 flux asks for 6 blocks per SM, which caps it at 80
+ * registers (a small spill) and was measured faster than 127 registers; the
+ * FP64 flux is bound by the FP64 pipe and keeps its registers */
 template <typename R, int M, int D, bool FLUX>
-__global__ void __launch_bounds__(128) face_flux_kernel(KP P, const double *__restrict__ W, const R *__restrict__ B,
+__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? 6 : 1)) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
                                                         const double *__restrict__ dtp, double *__restrict__ fs,
                                                         R *__restrict__ ff, int *__restrict__ status)
 {
     constexpr int NG = (M == 2) ? 2 : 4;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < P.nface[D] * NG) face_flux_item<R, M, D, FLUX>(P, W, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
+    if (t < P.nface[D] * NG) face_flux_item<R, M, D, FLUX>(P, src, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
 }
 
 /* ------------------------------------------------------------------ */
@@ -522,9 +554,68 @@ __device__ __forceinline__ long face_of(const KP &P, int d, int i, int j, int k,
 template <typename R, int M, int STAGE>
 __device__ __forceinline__ void update_item(const KP &P, const R *__restrict__ ff, double dt, double *__restrict__ W,
                                             double *__restrict__ G, double *__restrict__ Ws, double *__restrict__ Gs,
-                                            double *__restrict__ Acc, int *__restrict__ status, long cell)
+                                            double *__restrict__ Acc, const Shadow &s0, const Shadow &s1,
+                                            int *__restrict__ status, long cell)
 {
     constexpr int NV = M + 2, NG = (M == 1) ? 1 : ((M == 2) ? 2 : 4);
+    if constexpr (sizeof(R) == sizeof(float) && M >= 2) {
+        /* mixed precision: face sums in FP32 (the face values are FP32), the
+         * stage combination of the averages in FP64, the next stage's input
+         * as the FP32 shadow (s1 after stage 1, s0 after stage 2) */
+        const int i = (int)(cell % P.n[0]);
+        const int j = (int)((cell / P.n[0]) % P.n[1]);
+        const int k = (M >= 3) ? (int)(cell / ((long)P.n[0] * P.n[1])) : 0;
+        const long nft = P.nftot;
+        const float wg = 1.0f / NG, ihf = (float)P.ih;
+        long fp[M], fm[M];
+#pragma unroll
+        for (int d = 0; d < M; ++d) {
+            fp[d] = face_of<M>(P, d, i, j, k, 1);
+            fm[d] = face_of<M>(P, d, i, j, k, 0);
+        }
+        const Shadow &so = (STAGE == 1) ? s1 : s0;
+        double Wn[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            float DF = 0.f, DFt = 0.f;
+#pragma unroll
+            for (int d = 0; d < M; ++d) {
+                float Dh = 0.f;
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    const long o0 = ((long)(0 * NV + v) * NG + g) * nft, o1 = ((long)(1 * NV + v) * NG + g) * nft,
+                               o2 = ((long)(2 * NV + v) * NG + g) * nft;
+                    DF += (float)ff[o0 + fp[d]] - (float)ff[o0 + fm[d]];
+                    DFt += (float)ff[o1 + fp[d]] - (float)ff[o1 + fm[d]];
+                    Dh += (float)ff[o2 + fp[d]] - (float)ff[o2 + fm[d]];
+                }
+                const float gv = Dh * wg * ihf;
+                so.g[(d * NV + v) * P.ncell + cell] = gv;
+                if (STAGE == 2) G[(d * NV + v) * P.ncell + cell] = (double)gv;
+            }
+            const double dF = (double)(DF * wg * ihf), dFt = (double)(DFt * wg * ihf);
+            double w;
+            if (STAGE == 1) {
+                w = W[v * P.ncell + cell] - 0.5 * dt * dF - dt * dt * 0.125 * dFt;
+                Acc[v * P.ncell + cell] = -dt * dF - dt * dt / 6.0 * dFt;
+            } else {
+                w = W[v * P.ncell + cell] + Acc[v * P.ncell + cell] - dt * dt / 3.0 * dFt;
+                W[v * P.ncell + cell] = w;
+            }
+            split_store(w, so.hi, so.lo, v * P.ncell + cell);
+            Wn[v] = w;
+        }
+        double ke = 0.0;
+#pragma unroll
+        for (int a = 0; a < M; ++a) ke += Wn[1 + a] * Wn[1 + a];
+        const double p = (P.gamma - 1.0) * (Wn[M + 1] - 0.5 * ke / Wn[0]);
+        int st = 0;
+        if (!(Wn[0] > 0.0)) st |= ST_RHO;
+        if (!(p > 0.0)) st |= ST_P;
+        if (!isfinite(p) || !isfinite(Wn[0])) st |= ST_NAN;
+        if (st) atomicOr(status, st);
+        return;
+    }
     const int i = (int)(cell % P.n[0]);
     const int j = (M >= 2) ? (int)((cell / P.n[0]) % P.n[1]) : 0;
     const int k = (M >= 3) ? (int)(cell / ((long)P.n[0] * P.n[1])) : 0;
@@ -581,42 +672,62 @@ template <typename R, int M, int STAGE>
 __global__ void __launch_bounds__(256) update_kernel(KP P, const R *__restrict__ ff, const double *__restrict__ dtp,
                                                     double *__restrict__ W, double *__restrict__ G,
                                                     double *__restrict__ Ws, double *__restrict__ Gs,
-                                                    double *__restrict__ Acc, int *__restrict__ status)
+                                                    double *__restrict__ Acc, Shadow s0, Shadow s1,
+                                                    int *__restrict__ status)
 {
     const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell < P.ncell) update_item<R, M, STAGE>(P, ff, dtp[0], W, G, Ws, Gs, Acc, status, cell);
+    if (cell < P.ncell) update_item<R, M, STAGE>(P, ff, dtp[0], W, G, Ws, Gs, Acc, s0, s1, status, cell);
+}
+
+/* FP32 shadow of the FP64 state (after the state is set) */
+template <int M>
+__global__ void shadow_kernel(KP P, const double *__restrict__ W, const double *__restrict__ G, Shadow s)
+{
+    constexpr int NV = M + 2;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += (long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            split_store(W[v * P.ncell + c], s.hi, s.lo, v * P.ncell + c);
+#pragma unroll
+            for (int a = 0; a < M; ++a) s.g[(a * NV + v) * P.ncell + c] = (float)G[(a * NV + v) * P.ncell + c];
+        }
+    }
 }
 
 /* ------------------------------------------------------------------ */
 /* CFL time step on the device                                         */
 /* ------------------------------------------------------------------ */
-template <int M>
-__global__ void wavespeed_kernel(KP P, const double *__restrict__ W, unsigned long long *__restrict__ smax)
+/* max over cells of max_d |u_d| + c, read from the FP64 state (T = double)
+ * or from its FP32 shadow (T = float) */
+template <int M, typename T>
+__global__ void wavespeed_kernel(KP P, const T *__restrict__ W, unsigned long long *__restrict__ smax)
 {
-    double s = 0.0;
+    T s = T(0);
+    const T gam = T(P.gamma);
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += (long)gridDim.x * blockDim.x) {
-        const double rho = W[c];
-        double ke = 0.0, um = 0.0;
+        const T rho = W[c];
+        T ke = T(0), um = T(0);
 #pragma unroll
         for (int a = 0; a < M; ++a) {
-            const double u = W[(1 + a) * P.ncell + c] / rho;
+            const T u = W[(1 + a) * P.ncell + c] / rho;
             ke += u * u;
             um = fmax(um, fabs(u));
         }
-        const double p = (P.gamma - 1.0) * (W[(M + 1) * P.ncell + c] - 0.5 * rho * ke);
-        s = fmax(s, um + sqrt(P.gamma * p / rho));
+        const T p = (gam - T(1)) * (W[(M + 1) * P.ncell + c] - T(0.5) * rho * ke);
+        s = fmax(s, um + sqrt(gam * p / rho));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-    __shared__ double red[32];
+    __shared__ T red[32];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x < 32) {
-        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : T(0);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
         /* non-negative doubles order like their bit patterns; NaN is caught on the host */
-        if (threadIdx.x == 0) atomicMax(smax, (unsigned long long)__double_as_longlong(isnan(s) ? 1e300 : s));
+        const double sd = (double)s;
+        if (threadIdx.x == 0) atomicMax(smax, (unsigned long long)__double_as_longlong(isnan(sd) ? 1e300 : sd));
     }
 }
 

@@ -5,11 +5,24 @@
 
 namespace gks {
 
+template <typename R> Src<R> stage_src(gks_ctx *c, int input);
+template <> inline Src<double> stage_src<double>(gks_ctx *c, int input)
+{
+    return input ? Src<double>{c->Ws, c->Gs} : Src<double>{c->W, c->G};
+}
+template <> inline Src<float> stage_src<float>(gks_ctx *c, int input)
+{
+    const Shadow &s = input ? c->s1 : c->s0;
+    return Src<float>{s.hi, s.lo, s.g};
+}
+
 template <typename R, int M>
-static cudaError_t flux_impl(gks_ctx *c, const double *W, const double *G, double *fs_dev, bool flux)
+static cudaError_t flux_impl(gks_ctx *c, int input, double *fs_dev, bool flux)
 {
     const KP &P = c->kp;
     R *ff = (R *)c->ff;
+    const double *W = input ? c->Ws : c->W;
+    const double *G = input ? c->Gs : c->G;
     if constexpr (M == 1) {
         const unsigned nb = blocks_for(P.n[0] + 1);
         ProfScope ps(c, GKS_KC_FACE);
@@ -18,17 +31,18 @@ static cudaError_t flux_impl(gks_ctx *c, const double *W, const double *G, doubl
     } else {
         constexpr int NG = (M == 2) ? 2 : 4;
         R *B = (R *)c->B;
+        const Src<R> src = stage_src<R>(c, input);
         {
             ProfScope ps(c, GKS_KC_RECON);
-            cell_poly_kernel<R, M><<<blocks_for(P.next), kBlock, 0, c->stream>>>(P, W, G, B);
+            cell_poly_kernel<R, M><<<blocks_for(P.next), kBlock, 0, c->stream>>>(P, src, B);
         }
         for (int d = 0; d < M; ++d) {
             const unsigned nb = blocks_for(P.nface[d] * NG);
             ProfScope ps(c, GKS_KC_FACE);
 #define GKS_FACE(D)                                                                                           \
     if (d == D) {                                                                                             \
-        if (flux) face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, W, B, c->dt, nullptr, ff, c->status); \
-        else face_flux_kernel<R, M, D, false><<<nb, kBlock, 0, c->stream>>>(P, W, B, c->dt, fs_dev, nullptr, c->status); \
+        if (flux) face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+        else face_flux_kernel<R, M, D, false><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, fs_dev, nullptr, c->status); \
     }
             GKS_FACE(0)
             GKS_FACE(1)
@@ -39,14 +53,14 @@ static cudaError_t flux_impl(gks_ctx *c, const double *W, const double *G, doubl
     return cudaGetLastError();
 }
 
-template <int M> cudaError_t launch_states(gks_ctx *c, const double *W, const double *G, double *fs_dev)
+template <int M> cudaError_t launch_states(gks_ctx *c, int input, double *fs_dev)
 {
-    return c->precision ? flux_impl<float, M>(c, W, G, fs_dev, false) : flux_impl<double, M>(c, W, G, fs_dev, false);
+    return c->precision ? flux_impl<float, M>(c, input, fs_dev, false) : flux_impl<double, M>(c, input, fs_dev, false);
 }
 
-template <int M> cudaError_t launch_flux(gks_ctx *c, const double *W, const double *G)
+template <int M> cudaError_t launch_flux(gks_ctx *c, int input)
 {
-    return c->precision ? flux_impl<float, M>(c, W, G, nullptr, true) : flux_impl<double, M>(c, W, G, nullptr, true);
+    return c->precision ? flux_impl<float, M>(c, input, nullptr, true) : flux_impl<double, M>(c, input, nullptr, true);
 }
 
 template <typename R, int M> static cudaError_t update_impl(gks_ctx *c, int stage)
@@ -56,9 +70,11 @@ template <typename R, int M> static cudaError_t update_impl(gks_ctx *c, int stag
     const R *ff = (const R *)c->ff;
     ProfScope ps(c, GKS_KC_UPDATE);
     if (stage == 1)
-        update_kernel<R, M, 1><<<nb, 256, 0, c->stream>>>(P, ff, c->dt, c->W, c->G, c->Ws, c->Gs, c->Acc, c->status);
+        update_kernel<R, M, 1><<<nb, 256, 0, c->stream>>>(P, ff, c->dt, c->W, c->G, c->Ws, c->Gs, c->Acc, c->s0, c->s1,
+                                                          c->status);
     else
-        update_kernel<R, M, 2><<<nb, 256, 0, c->stream>>>(P, ff, c->dt, c->W, c->G, c->Ws, c->Gs, c->Acc, c->status);
+        update_kernel<R, M, 2><<<nb, 256, 0, c->stream>>>(P, ff, c->dt, c->W, c->G, c->Ws, c->Gs, c->Acc, c->s0, c->s1,
+                                                          c->status);
     return cudaGetLastError();
 }
 
@@ -78,15 +94,26 @@ template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl)
     long cap = (long)nsm * 8;
     const unsigned nb = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
     ProfScope ps(c, GKS_KC_DT);
-    wavespeed_kernel<M><<<nb, 256, 0, c->stream>>>(c->kp, c->W, c->smax);
+    if (c->shadows) wavespeed_kernel<M, float><<<nb, 256, 0, c->stream>>>(c->kp, c->s0.hi, c->smax);
+    else wavespeed_kernel<M, double><<<nb, 256, 0, c->stream>>>(c->kp, c->W, c->smax);
     if (cfl > 0.0) dt_from_speed_kernel<<<1, 1, 0, c->stream>>>(c->smax, cfl * c->h, c->dt);
     return cudaGetLastError();
 }
 
+template <int M> cudaError_t launch_shadow(gks_ctx *c)
+{
+    if (!c->shadows) return cudaSuccess;
+    const long want = (c->kp.ncell + 255) / 256;
+    shadow_kernel<M><<<(unsigned)(want < 4096 ? (want > 0 ? want : 1) : 4096), 256, 0, c->stream>>>(c->kp, c->W, c->G,
+                                                                                                   c->s0);
+    return cudaGetLastError();
+}
+
 #define GKS_INSTANTIATE(M)                                                                                \
-    template cudaError_t launch_states<M>(gks_ctx *, const double *, const double *, double *);          \
-    template cudaError_t launch_flux<M>(gks_ctx *, const double *, const double *);                      \
+    template cudaError_t launch_states<M>(gks_ctx *, int, double *);                                      \
+    template cudaError_t launch_flux<M>(gks_ctx *, int);                                                  \
     template cudaError_t launch_update<M>(gks_ctx *, int);                                                \
-    template cudaError_t launch_wavespeed<M>(gks_ctx *, double);
+    template cudaError_t launch_wavespeed<M>(gks_ctx *, double);                                          \
+    template cudaError_t launch_shadow<M>(gks_ctx *);
 
 } // namespace gks

@@ -108,11 +108,12 @@ extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e == cudaSuccess) {
         gks::set_scalar_kernel<<<1, 1, 0, s>>>(dtp, dt);
-        gks::cell_poly_kernel<double, 2><<<gks::blocks_for(P.next), gks::kBlock, 0, s>>>(P, W, G, B);
+        const gks::Src<double> src{W, G};
+        gks::cell_poly_kernel<double, 2><<<gks::blocks_for(P.next), gks::kBlock, 0, s>>>(P, src, B);
         gks::face_flux_kernel<double, 2, 0, true>
-            <<<gks::blocks_for(P.nface[0] * 2), gks::kBlock, 0, s>>>(P, W, B, dtp, nullptr, face_flux, status);
+            <<<gks::blocks_for(P.nface[0] * 2), gks::kBlock, 0, s>>>(P, src, B, dtp, nullptr, face_flux, status);
         gks::face_flux_kernel<double, 2, 1, true>
-            <<<gks::blocks_for(P.nface[1] * 2), gks::kBlock, 0, s>>>(P, W, B, dtp, nullptr, face_flux, status);
+            <<<gks::blocks_for(P.nface[1] * 2), gks::kBlock, 0, s>>>(P, src, B, dtp, nullptr, face_flux, status);
         e = cudaGetLastError();
     }
     int st = 0;
