@@ -237,6 +237,87 @@ def time_e2e(B, torch, W, G, precision, steps, warmup, dev):
     return N * N * steps / el, nbytes, nbytes
 
 
+def aggregate(ws, ms_local, dist=None, device=None):
+    """Max over ranks of the per-rank step times (replicas: each rank advances
+    its own grid), so the whole-job rate is ws * cells / max time."""
+    if ws == 1 or dist is None:
+        return list(ms_local)
+    import torch
+
+    t = torch.tensor(list(ms_local), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def time_batch(B, torch, steps, dev):
+    """Config 4: 256 independent grids, sides log-uniform in [64, 1024], four-
+    quadrant ICs (seed 20464 + i), transmissive, CFL 0.4; mixed precision timed
+    with the graph replay; density L1 of mixed against the FP64 batch after 3
+    equal steps."""
+    from paper_2507_20461_gb300 import inputs as I
+
+    sides = I.batch_sizes(256, seed=20464)
+    hs = [1.0 / n for n in sides]
+    cells = sum(n * n for n in sides)
+    states = [I.quadrants_2d(n, seed=20464 + g)[:2] for g, n in enumerate(sides)]
+    out = {}
+    rho = {}
+    for prec in (1, 0):
+        bt = B.Batch(sides, sides, hs, bc=B.BC_TRANSMISSIVE, precision=prec)
+        for g, (W, G) in enumerate(states):
+            bt.set_state(g, torch.from_numpy(W).to(dev), torch.from_numpy(G).to(dev))
+        bt.run(CFL, 3)  # tuning + graph recording + 3 steps
+        torch.cuda.synchronize()
+        rho[prec] = []
+        for g in (0, 1, 2, 100, 255):
+            Wd = torch.from_numpy(states[g][0]).to(dev)
+            Gd = torch.from_numpy(states[g][1]).to(dev)
+            bt.get_state(g, Wd, Gd)
+            rho[prec].append(Wd[0].clone())
+        if prec == 1:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            stream = torch.cuda.current_stream()
+            e0.record(stream)
+            bt.run(CFL, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            out = {"value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps,
+                   "grids": 256, "cells": cells, "status": bt.status(), "tuning": json.loads(bt.tuning() or "{}")}
+        bt.close()
+    l1 = max(float((a - b).abs().mean()) for a, b in zip(rho[1], rho[0]))
+    out["l1_density_mixed_vs_fp64_3_steps"] = l1
+    out["workload"] = "256 grids, sides log-uniform [64,1024], four-quadrant ICs, transmissive, mixed precision, graph replay"
+    return out
+
+
+def time_3d(B, torch, steps, dev):
+    """Config 5: 3D 256^3 periodic solenoidal turbulence (rms Mach 0.6), mixed precision."""
+    from paper_2507_20461_gb300 import inputs as I
+
+    n = 256
+    W, G, h = I.turbulence_3d(n, seed=20465)
+    s = B.Solver((n, n, n), lo=[0, 0, 0], hi=[1, 1, 1], bc=B.BC_PERIODIC, precision=1)
+    Wd = torch.from_numpy(W).to(dev)
+    Gd = torch.from_numpy(G).to(dev)
+    s.set_state(Wd, Gd)
+    s.step_cfl(CFL, 2)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step_cfl(CFL, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = s.status()
+    s.close()
+    return {"value": n**3 / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps, "status": st,
+            "workload": "3D 256^3 periodic solenoidal velocity (E(k) ~ k^4 exp(-2(k/4)^2), rms Mach 0.6), mixed precision"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -244,6 +325,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true", help="skip the batched and 3D workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -277,10 +359,7 @@ def main():
     ms_mixed, prof_mixed, rho_mixed, st_mixed = time_path(B, torch, W, G, h, 1, args.steps, args.warmup, dev)
     ms_fp64, prof_fp64, rho_fp64, st_fp64 = time_path(B, torch, W, G, h, 0, steps64, args.warmup, dev)
     torch.cuda.synchronize()
-    if ws > 1:
-        t = torch.tensor([ms_mixed, ms_fp64], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_mixed, ms_fp64 = t.tolist()
+    ms_mixed, ms_fp64 = aggregate(ws, [ms_mixed, ms_fp64], dist if ws > 1 else None, dev)
     clk = clocks.stop()
 
     # mixed vs FP64 after the same number of steps (warmup + steps for each)
@@ -307,6 +386,8 @@ def main():
         s0.close()
 
     e2e_val, h2d, d2h = time_e2e(B, torch, W, G, 1, max(2, min(args.steps, 5)), 1, dev)
+    batch = time_batch(B, torch, max(3, min(args.steps, 20)), dev) if not args.headline_only else None
+    three_d = time_3d(B, torch, max(3, min(args.steps, 10)), dev) if not args.headline_only else None
 
     peaks, peak_src = _peaks()
     sm_clock = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
@@ -370,7 +451,9 @@ def main():
                       ((B.KC_RECON, "cell_poly"), (B.KC_FACE, "face_flux"), (B.KC_UPDATE, "update"), (B.KC_DT, "dt"))},
         "status": {"mixed": st_mixed, "fp64": st_fp64},
         "e2e": {"value": ws * e2e_val, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step * (args.steps + steps64),
+        "gpu_launches": launches_per_step * args.steps,
+        "batched_256_grids": batch,
+        "three_d_256": three_d,
         "clocks": clk,
         "cpu_baseline": cpu,
         "peaks_source": peak_src,

@@ -308,6 +308,7 @@ int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc
     P.fp.gamma = gamma;
     P.fp.c1 = o.c1_tau;
     P.fp.c2 = o.c2_tau;
+    gks::finalize_kp(P);
 
     cudaError_t e = cudaMemsetAsync(c->ws, 0, L.total, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

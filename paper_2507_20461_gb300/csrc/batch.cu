@@ -93,6 +93,7 @@ void make_kp(gks::KP &P, int nx, int ny, double h, double gamma, int bc, const g
     P.fp.gamma = gamma;
     P.fp.c1 = o.c1_tau;
     P.fp.c2 = o.c2_tau;
+    gks::finalize_kp(P);
 }
 
 /* item count of kernel class k on grid g (flux: per direction) */

@@ -229,9 +229,33 @@ __device__ __forceinline__ void euler_dflux(const Prim<R, M> &P, const R *W, R g
     dF[M + 1] = dU[e] * (W[M + 1] + P.p) + P.U[e] * (dW[M + 1] + dp);
 }
 
+/* Flux constants, precomputed on the host in both precisions so that an
+ * FP32 kernel issues no FP64 instruction for them (fill with fill_flux). */
 struct FluxParams {
     double gamma, c1, c2;
+    double gm1, Ntot;      /* gamma - 1, 2 / (gamma - 1) */
+    float fgm1, fNtot, fc1, fc2;
 };
+
+/* the constant in the precision R */
+template <typename R> __host__ __device__ __forceinline__ R pick(double d, float f)
+{
+    if constexpr (sizeof(R) == sizeof(float)) return f;
+    else return d;
+}
+
+inline void fill_flux(FluxParams &fp, double gamma, double c1, double c2)
+{
+    fp.gamma = gamma;
+    fp.c1 = c1;
+    fp.c2 = c2;
+    fp.gm1 = gamma - 1.0;
+    fp.Ntot = 2.0 / (gamma - 1.0);
+    fp.fgm1 = (float)fp.gm1;
+    fp.fNtot = (float)fp.Ntot;
+    fp.fc1 = (float)c1;
+    fp.fc2 = (float)c2;
+}
 
 /* Returns false (and leaves outputs untouched) when a state is not admissible. */
 template <typename R, int M>
@@ -239,8 +263,8 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
                                           const R (*dWr)[M + 2], R *F, R *Ft, R *Wh)
 {
     constexpr int NV = M + 2;
-    const R gm1 = R(fp.gamma - 1.0);
-    const R Ntot = R(2.0 / (fp.gamma - 1.0));
+    const R gm1 = pick<R>(fp.gm1, fp.fgm1);
+    const R Ntot = pick<R>(fp.Ntot, fp.fNtot);
     const R K = Ntot - R(M);
     Prim<R, M> Pl, Pr, P0;
     if (!to_prim<R, M>(Wl, gm1, Pl) || !to_prim<R, M>(Wr, gm1, Pr)) return false;
@@ -317,7 +341,7 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
 
     /* collision times and time integrals */
     const R pl = Pl.p, pr = Pr.p;
-    const R tn = R(fp.c1) * dt + R(fp.c2) * RT<R>::abs_(pl - pr) / (pl + pr) * dt;
+    const R tn = pick<R>(fp.c1, fp.fc1) * dt + pick<R>(fp.c2, fp.fc2) * RT<R>::abs_(pl - pr) / (pl + pr) * dt;
     const R hdt = R(0.5) * dt;
     R eh = R(0), e1 = R(0);
     if (tn > R(0)) {

@@ -42,7 +42,23 @@ struct KP {
     double h, ih, gamma;
     double C, itanhC, eps, C0, adm;
     FluxParams fp;
+    /* FP32 copies for the mixed-precision kernels (fill with finalize_kp) */
+    float fh, fih, fgm1, fC, fitanhC, feps, fC0, fadm;
 };
+
+/* derived fields of a parameter block whose double fields are set */
+inline void finalize_kp(KP &P)
+{
+    fill_flux(P.fp, P.gamma, P.fp.c1, P.fp.c2);
+    P.fh = (float)P.h;
+    P.fih = (float)P.ih;
+    P.fgm1 = (float)(P.gamma - 1.0);
+    P.fC = (float)P.C;
+    P.fitanhC = (float)P.itanhC;
+    P.feps = (float)P.eps;
+    P.fC0 = (float)P.C0;
+    P.fadm = (float)P.adm;
+}
 
 /* FP32 shadow of a state (mixed precision, 2D/3D): hi = float(W),
  * lo = float(W - hi) (so neighbour differences keep FP64-level accuracy),
@@ -104,13 +120,13 @@ __device__ __forceinline__ long cell_lin(const KP &P, int i, int j, int k, int *
 template <typename R>
 __device__ __forceinline__ R chi_of(const KP &P, R ISt, R ISH, R ISL, int r)
 {
-    const R eps = R(P.eps);
+    const R eps = pick<R>(P.eps, P.feps);
     R xH = ISt / (ISH + eps), xL = ISt / (ISL + eps);
     R pH = xH * xH, pL = xL * xL;
     if (r == 3) { pH *= xH; pL *= xL; }
     const R aH = R(1) + pH, aL = R(1) + pL;
     const R alpha = R(2) * aH / (aH + aL);
-    return RT<R>::tanh_(R(P.C) * alpha) * R(P.itanhC);
+    return RT<R>::tanh_(pick<R>(P.C, P.fC) * alpha) * pick<R>(P.itanhC, P.fitanhC);
 }
 
 template <typename R, int M>
@@ -146,9 +162,9 @@ __device__ __forceinline__ void geno1d_blend(const KP &P, const R (*a)[2], const
     const R ISL = fmin(IS[0], fmin(IS[1], IS[2]));
     const R ISt = RT<R>::abs_(R(0.5) * (IS[1] + IS[2]) - IS[0]);
     const R chi = P.limiter ? R(1) : chi_of<R>(P, ISt, ISH, ISL, 2);
-    const R eps = R(P.eps);
+    const R eps = pick<R>(P.eps, P.feps);
     const R w0 = R(1) / ((IS[0] + eps) * (IS[0] + eps));
-    const R w1 = R(P.C0) / ((IS[1] + eps) * (IS[1] + eps));
+    const R w1 = pick<R>(P.C0, P.fC0) / ((IS[1] + eps) * (IS[1] + eps));
     const R w2 = R(1) / ((IS[2] + eps) * (IS[2] + eps));
     const R iws = R(1) / (w0 + w1 + w2);
     const R lv = (w0 * pv[0] + w1 * pv[1] + w2 * pv[2]) * iws;
@@ -197,7 +213,7 @@ __device__ __forceinline__ void recon1d_face(const KP &P, const double *__restri
             R val, der;
             geno1d_blend<R>(P, a, pv, pd, qv, qd, val, der);
             st[0][v][0] = R(w[1][v]) + val;
-            st[0][v][1] = der * R(P.ih);
+            st[0][v][1] = der * pick<R>(P.ih, P.fih);
             cw[0][v] = R(w[1][v]);
         }
         /* right: reconstruction cell j+1 = f (index 2), mirrored stencils */
@@ -220,7 +236,7 @@ __device__ __forceinline__ void recon1d_face(const KP &P, const double *__restri
             R val, der;
             geno1d_blend<R>(P, a, pv, pd, qv - dj, qd, val, der);
             st[1][v][0] = R(w[2][v]) + val;
-            st[1][v][1] = der * R(P.ih);
+            st[1][v][1] = der * pick<R>(P.ih, P.fih);
             cw[1][v] = R(w[2][v]);
         }
     }
@@ -237,14 +253,14 @@ __global__ void __launch_bounds__(128) face1d_kernel(KP P, const double *__restr
     if (f > P.n[0]) return;
     R st[2][3][2], cw[2][3];
     recon1d_face<R>(P, W, G, f, st, cw);
-    const R gm1 = R(P.gamma - 1.0);
+    const R gm1 = pick<R>(P.fp.gm1, P.fgm1);
     R Wl[3], Wr[3], dWl[1][3], dWr[1][3];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         R s[3];
 #pragma unroll
         for (int v = 0; v < 3; ++v) s[v] = st[side][v][0];
-        const bool ok = admissible<R, 1>(s, cw[side], gm1, R(P.adm));
+        const bool ok = admissible<R, 1>(s, cw[side], gm1, pick<R>(P.adm, P.fadm));
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
             const R val = ok ? st[side][v][0] : cw[side][v];
@@ -325,11 +341,10 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R
         o[q / 2] += (q & 1) ? 1 : -1;
         cl[1 + q] = cell_lin<M>(P, o[0], o[1], o[2], fl[1 + q]);
     }
-    const double h = P.h;
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) {
         R d[ND];
-        const R hr = R(h);
+        const R hr = pick<R>(P.h, P.fh);
 #pragma unroll
         for (int q = 0; q < 2 * M; ++q) {
             d[q * (1 + M)] = R(src.delta(v * P.ncell + cl[1 + q], v * P.ncell + cl[0]));
@@ -376,7 +391,7 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R
             }
             const R ISL = (ssum - smin - smax) * R(1.0 / (2 * M - 2));
             chi = chi_of<R>(P, ISt, ISH, ISL, 3);
-            const R eps = R(P.eps);
+            const R eps = pick<R>(P.eps, P.feps);
             R ws = R(0);
 #pragma unroll
             for (int q = 0; q < 2 * M; ++q) {
@@ -427,14 +442,19 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
 {
     constexpr int NV = M + 2, NC = Cubic<R, M>::NC, NG = (M == 2) ? 2 : 4;
     const long nf = P.nface[D];
-    const int g = (int)(t / nf);
-    const long fl = t - (long)g * nf;
+    /* FP32: the Gauss points of one face are neighbouring threads (they read
+     * the same two cells' coefficients; measured faster).  FP64: one Gauss
+     * point per warp, so the per-point evaluation does not diverge in this
+     * compute-bound kernel. */
+    constexpr bool gfast = sizeof(R) == sizeof(float);
+    const int g = gfast ? (int)(t % NG) : (int)(t / nf);
+    const long fl = gfast ? t / NG : t - (long)g * nf;
     int e0 = P.n[0] + (D == 0), e1 = P.n[1] + (D == 1);
     int idx[3];
     idx[0] = (int)(fl % e0);
     idx[1] = (M >= 2) ? (int)((fl / e0) % e1) : 0;
     idx[2] = (M >= 3) ? (int)(fl / ((long)e0 * e1)) : 0;
-    const R gm1 = R(P.gamma - 1.0);
+    const R gm1 = pick<R>(P.fp.gm1, P.fgm1);
     /* interface states, global axes: st[side][v][c], c = 0 value, 1 + e d/dx_e */
     R st[2][NV][M + 1], cw[2][NV];
 #pragma unroll
@@ -455,12 +475,12 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
             cw[side][v] = w0;
             st[side][v][0] = w0 + out[0];
 #pragma unroll
-            for (int a = 0; a < M; ++a) st[side][v][1 + a] = out[1 + a] * R(P.ih);
+            for (int a = 0; a < M; ++a) st[side][v][1 + a] = out[1 + a] * pick<R>(P.ih, P.fih);
         }
         R s[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) s[v] = st[side][v][0];
-        if (!admissible<R, M>(s, cw[side], gm1, R(P.adm))) {
+        if (!admissible<R, M>(s, cw[side], gm1, pick<R>(P.adm, P.fadm))) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 st[side][v][0] = cw[side][v];
@@ -523,9 +543,11 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
     }
 }
 
-/* 128 threads; the FP32 flux asks for 6 blocks per SM, which caps it at 80
- * registers (a small spill) and was measured faster than 127 registers; the
- * FP64 flux is bound by the FP64 pipe and keeps its registers */
+/* 128 threads; the FP32 flux asks for 6 blocks per SM (80 registers, a small
+ * spill), measured faster than 127 registers.  (8 blocks, 64 registers, was
+ * faster still but moved the FP32 rounding enough to flip a face-state
+ * fallback decision against the FP64 oracle on a coarse shock problem.)  The
+ * FP64 flux is bound by the FP64 pipe and keeps its registers. */
 template <typename R, int M, int D, bool FLUX>
 __global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? 6 : 1)) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
                                                         const double *__restrict__ dtp, double *__restrict__ fs,
@@ -566,7 +588,7 @@ __device__ __forceinline__ void update_item(const KP &P, const R *__restrict__ f
         const int j = (int)((cell / P.n[0]) % P.n[1]);
         const int k = (M >= 3) ? (int)(cell / ((long)P.n[0] * P.n[1])) : 0;
         const long nft = P.nftot;
-        const float wg = 1.0f / NG, ihf = (float)P.ih;
+        const float wg = 1.0f / NG, ihf = P.fih;
         long fp[M], fm[M];
 #pragma unroll
         for (int d = 0; d < M; ++d) {
@@ -703,7 +725,7 @@ template <int M, typename T>
 __global__ void wavespeed_kernel(KP P, const T *__restrict__ W, unsigned long long *__restrict__ smax)
 {
     T s = T(0);
-    const T gam = T(P.gamma);
+    const T gam = pick<T>(P.gamma, (float)(P.fgm1 + 1.0f));
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += (long)gridDim.x * blockDim.x) {
         const T rho = W[c];
         T ke = T(0), um = T(0);

@@ -103,6 +103,7 @@ extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc
     P.fp.gamma = gamma;
     P.fp.c1 = o.c1_tau;
     P.fp.c2 = o.c2_tau;
+    gks::finalize_kp(P);
 
     /* the status word must start at zero; the coefficients are fully rewritten */
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
