@@ -262,17 +262,23 @@ def time_batch(B, torch, steps, dev):
     states = [I.quadrants_2d(n, seed=20464 + g)[:2] for g, n in enumerate(sides)]
     out = {}
     rho = {}
+    sample = (0, 1, 2, 100, 255)
     for prec in (1, 0):
-        bt = B.Batch(sides, sides, hs, bc=B.BC_TRANSMISSIVE, precision=prec)
-        for g, (W, G) in enumerate(states):
-            bt.set_state(g, torch.from_numpy(W).to(dev), torch.from_numpy(G).to(dev))
+        # mixed: all 256 grids (timed); FP64 reference: the sampled grids only
+        # (grids are independent, so their results do not depend on the rest)
+        ids = list(range(len(sides))) if prec == 1 else list(sample)
+        bt = B.Batch([sides[g] for g in ids], [sides[g] for g in ids], [hs[g] for g in ids],
+                     bc=B.BC_TRANSMISSIVE, precision=prec)
+        for k, g in enumerate(ids):
+            W, G = states[g]
+            bt.set_state(k, torch.from_numpy(W).to(dev), torch.from_numpy(G).to(dev))
         bt.run(CFL, 3)  # tuning + graph recording + 3 steps
         torch.cuda.synchronize()
         rho[prec] = []
-        for g in (0, 1, 2, 100, 255):
+        for g in sample:
             Wd = torch.from_numpy(states[g][0]).to(dev)
             Gd = torch.from_numpy(states[g][1]).to(dev)
-            bt.get_state(g, Wd, Gd)
+            bt.get_state(ids.index(g), Wd, Gd)
             rho[prec].append(Wd[0].clone())
         if prec == 1:
             e0 = torch.cuda.Event(enable_timing=True)
