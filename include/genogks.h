@@ -71,7 +71,18 @@ typedef struct {
     double hi[3];    /*   on all active axes                                     */
 } gks_grid_t;
 
-typedef enum { GKS_BC_PERIODIC = 0, GKS_BC_TRANSMISSIVE = 1 } gks_bc_t;
+/* Boundary condition on every side, by ghost cells that are index maps:
+ * periodic wraps; transmissive mirrors every variable evenly (the normal
+ * derivative changes sign); reflective (a slip wall) mirrors likewise but
+ * negates the momentum normal to the wall (used by the paper's blast wave,
+ * Sec. 6.6); no-slip (an adiabatic wall at rest, for the Navier-Stokes
+ * equations, Sec. 6.9) negates every momentum component. */
+typedef enum {
+    GKS_BC_PERIODIC = 0,
+    GKS_BC_TRANSMISSIVE = 1,
+    GKS_BC_REFLECTIVE = 2,
+    GKS_BC_NOSLIP = 3
+} gks_bc_t;
 
 typedef struct {
     int precision;    /* 0: FP64 throughout; 1: reconstruction and flux in FP32,
@@ -88,6 +99,11 @@ typedef struct {
     void *stream;     /* cudaStream_t for all work; NULL = legacy default stream */
     void *workspace;  /* optional caller-owned device memory for all buffers     */
     size_t workspace_bytes; /* its size; see gks_workspace_bytes                 */
+    double mu;        /* dynamic viscosity: 0 solves the Euler equations; > 0 the
+                         Navier-Stokes equations with Prandtl number 1 (Sec. 2,
+                         Sec. 6.9): physical collision time mu / p in the BGK
+                         solution, added to tau_n, and the viscous time-step
+                         limit in gks_step_cfl (0)                               */
 } gks_opts_t;
 
 typedef struct gks_ctx *gks_handle_t;
@@ -103,8 +119,9 @@ size_t gks_workspace_bytes(const gks_grid_t *grid, int precision);
 /* Number of faces F (all directions) of the grid; -1 on a bad grid. */
 long gks_face_count(const gks_grid_t *grid);
 
-/* Create a solver for the Euler equations with ratio of specific heats gamma
- * (> 1) on `grid` with boundary condition `bc` on every side.
+/* Create a solver for the Euler equations (opts->mu = 0) or the Navier-Stokes
+ * equations (opts->mu > 0) with ratio of specific heats gamma (> 1) on `grid`
+ * with boundary condition `bc` on every side.
  * order: 8 in 1D (Sec. 4.2), 4 in 2D/3D (Sec. 4.3); anything else gives
  * GKS_ERR_UNSUPPORTED.  opts may be NULL (defaults).  If opts->workspace is
  * given it must hold gks_workspace_bytes bytes (else GKS_ERR_OOM) and the
@@ -146,7 +163,9 @@ int gks_flux(gks_handle_t h, double dt, double *face_flux, int on_device);
 int gks_step(gks_handle_t h, double dt);
 
 /* nsteps steps, each with dt = cfl h / max_cells max_d(|u_d| + c) computed on
- * the device (no host round trip).  Asynchronous. */
+ * the device (no host round trip); with opts->mu > 0 also at most
+ * cfl h^2 / (2 (m - 1) nu_max), nu_max = mu / min_cells rho (Sec. 6; the
+ * factor 2 (m - 1) is taken as 2 in 1D).  Asynchronous. */
 int gks_step_cfl(gks_handle_t h, double cfl, int nsteps);
 
 /* max over cells and axes of |u_d| + c of the current state.  Synchronises. */
@@ -201,7 +220,8 @@ const char *gks_last_error(gks_handle_t h);
  * (nx + 2) * (ny + 2) <= 14400 cells including the one-cell ghost ring (for
  * example 118 x 118); larger grids return
  * GKS_ERR_ARG, as do invalid sizes, gamma, bc, dt or NULL pointers.
- * GKS_ERR_UNSUPPORTED: precision != 0.  GKS_ERR_NONPHYSICAL: a face state the
+ * GKS_ERR_UNSUPPORTED: precision != 0 or mu != 0 (Euler flux only).
+ * GKS_ERR_NONPHYSICAL: a face state the
  * flux could not use.  GKS_ERR_CUDA: a CUDA call failed.
  *
  * The first call on a device looks up the device address of that array
@@ -222,7 +242,8 @@ typedef struct gks_batch_ctx *gks_batch_t;
  * Every grid keeps its own CFL time step.  opts may be NULL; opts->precision
  * and the scheme constants apply to every grid, opts->stream orders the
  * batch's work after the caller's (the batch runs on an internal stream that
- * can be captured); opts->workspace is not supported (GKS_ERR_UNSUPPORTED).
+ * can be captured); opts->workspace and opts->mu != 0 (the Euler flux only)
+ * are not supported (GKS_ERR_UNSUPPORTED).
  * The library allocates one device buffer for all grids. */
 int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs, double gamma, gks_bc_t bc,
                      const gks_opts_t *opts, gks_batch_t *out);

@@ -40,6 +40,7 @@ class Cfg(C.Structure):
         ("limiter", C.c_int),
         ("tau_mode", C.c_int),
         ("adm_delta", C.c_double),
+        ("mu", C.c_double),
     ]
 
 
@@ -72,7 +73,9 @@ def lib():
         L.or_geno1d_point.argtypes = [cp, dp, dp, C.c_int, dp]
         L.or_genomd_cell.argtypes = [cp, dp, dp]
         L.or_monomials.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int)]
-        L.or_gks_point.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp]
+        L.or_gks_point.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, dp, dp, dp, dp, dp, dp, dp]
+        L.or_max_kin_viscosity.argtypes = [cp, dp]
+        L.or_max_kin_viscosity.restype = C.c_double
         L.or_slope_solve.argtypes = [C.c_int, C.c_double, dp, dp, dp]
         L.or_moment_matrix.argtypes = [C.c_int, C.c_double, dp, dp]
         L.or_mom_half.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int]
@@ -86,9 +89,11 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def make_cfg(dim, n, h, gamma=1.4, bc=0, C_=20.0, eps=1e-15, C0=8.0, c1_tau=0.05, c2_tau=1.0, limiter=0, tau_mode=0, adm_delta=0.3) -> Cfg:
+def make_cfg(dim, n, h, gamma=1.4, bc=0, C_=20.0, eps=1e-15, C0=8.0, c1_tau=0.05, c2_tau=1.0, limiter=0, tau_mode=0, adm_delta=0.3, mu=0.0) -> Cfg:
     nn = list(n) + [1] * (3 - len(n))
-    return Cfg(dim, (C.c_int * 3)(*nn), h, gamma, bc, C_, eps, C0, c1_tau, c2_tau, limiter, tau_mode, adm_delta)
+    if mu > 0.0 and tau_mode == 0:
+        tau_mode = 2
+    return Cfg(dim, (C.c_int * 3)(*nn), h, gamma, bc, C_, eps, C0, c1_tau, c2_tau, limiter, tau_mode, adm_delta, mu)
 
 
 def ngauss(dim: int) -> int:
@@ -137,6 +142,21 @@ def max_wavespeed(cfg: Cfg, W: np.ndarray) -> float:
     return float(lib().or_max_wavespeed(C.byref(cfg), _p(W)))
 
 
+def max_kin_viscosity(cfg: Cfg, W: np.ndarray) -> float:
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    return float(lib().or_max_kin_viscosity(C.byref(cfg), _p(W)))
+
+
+def cfl_dt(cfg: Cfg, W: np.ndarray, cfl: float) -> float:
+    """CFL time step with the viscous limit cfl h^2 / (2 (m - 1) nu) (Sec. 6;
+    2 nu in 1D) when mu > 0."""
+    dt = cfl * cfg.h / max_wavespeed(cfg, W)
+    if cfg.mu > 0.0:
+        nu = max_kin_viscosity(cfg, W)
+        dt = min(dt, cfl * cfg.h * cfg.h / (2.0 * max(cfg.dim - 1, 1) * nu))
+    return dt
+
+
 def geno1d_point(cfg: Cfg, w5, d5, side: int) -> dict:
     w5 = np.ascontiguousarray(w5, dtype=np.float64)
     d5 = np.ascontiguousarray(d5, dtype=np.float64)
@@ -174,7 +194,7 @@ def genomd_cell(cfg: Cfg, W0, D0, Wn, Dn) -> dict:
     }
 
 
-def gks_point(m, gamma, dt, Wl, Wr, dWl, dWr, c1=0.05, c2=1.0, tau_mode=0):
+def gks_point(m, gamma, dt, Wl, Wr, dWl, dWr, c1=0.05, c2=1.0, tau_mode=0, mu=0.0):
     nv = m + 2
     Wl = np.ascontiguousarray(Wl, dtype=np.float64)
     Wr = np.ascontiguousarray(Wr, dtype=np.float64)
@@ -183,7 +203,7 @@ def gks_point(m, gamma, dt, Wl, Wr, dWl, dWr, c1=0.05, c2=1.0, tau_mode=0):
     F = np.zeros(nv)
     Ft = np.zeros(nv)
     Wh = np.zeros(nv)
-    r = lib().or_gks_point(m, gamma, c1, c2, int(tau_mode), dt, _p(Wl), _p(Wr), _p(dWl), _p(dWr), _p(F), _p(Ft), _p(Wh))
+    r = lib().or_gks_point(m, gamma, c1, c2, int(tau_mode), float(mu), dt, _p(Wl), _p(Wr), _p(dWl), _p(dWr), _p(F), _p(Ft), _p(Wh))
     if r != OK:
         raise RuntimeError("gks_point failed")
     return F, Ft, Wh

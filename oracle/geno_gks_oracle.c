@@ -38,12 +38,16 @@
  *       from the mean of the left/right derivatives; the numerical collision
  *       time tau_n = C1 dt + C2 |pl - pr| / (pl + pr) dt enters only the
  *       exponential relaxation, the physical one (0 for the Euler equations)
- *       the Chapman-Enskog terms (C1 = 0.05, C2 = 1);
+ *       the Chapman-Enskog terms (C1 = 0.05, C2 = 1); for the Navier-Stokes
+ *       equations the physical one is mu / p0 (Prandtl number 1) and is added
+ *       to tau_n;
  *   R7  two-stage fourth-order update with F and dF/dt recovered from the
  *       time-integrated fluxes over dt/2 and dt; the cell-averaged gradients
  *       are refreshed from the interface states at dt/2 of each stage
  *       (Eq. slope, Gauss theorem);
  *   R8  transmissive ghosts are the even extension (normal gradient negated),
+ *       reflective ghosts also negate the normal momentum (an odd component),
+ *       no-slip walls negate every momentum component,
  *       periodic ghosts wrap;
  *   R9  a reconstructed interface state whose density or pressure is not
  *       above 0.3 times that of its cell average falls back to the cell
@@ -74,15 +78,17 @@ typedef struct {
     int n[3];
     double h;
     double gamma;
-    int bc; /* 0 periodic, 1 transmissive */
+    int bc; /* 0 periodic, 1 transmissive, 2 reflective (slip), 3 no-slip wall */
     double C;      /* path-function steepness, Eq. HLP-weight: 20 */
     double eps;    /* Eq. HLP-sp: 1e-15 */
     double C0;     /* central sub-stencil weight, Sec. 3.3: 8 */
     double c1_tau; /* R6 */
     double c2_tau; /* R6 */
     int limiter;   /* 0 GENO, 1 linear (chi = 1) */
-    int tau_mode;  /* 0: Euler (physical tau = 0); 1: tau = tau_n (plain BGK) */
+    int tau_mode;  /* 0: Euler (physical tau = 0); 1: tau = tau_n (plain BGK);
+                      2: Navier-Stokes, physical tau = mu / p0, tau_n = tau + ... */
     double adm_delta; /* R9 admissibility fraction: 0.3 */
+    double mu;     /* dynamic viscosity for tau_mode 2 */
 } or_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -597,7 +603,7 @@ static void vp_mom_psi(const vpoly *X, const maxw *g, int half, int with_u, doub
 /* One interface Gauss point in the face frame (velocity component 0 and
  * derivative axis 0 are along the face normal).  dWl[e][a]: derivative of
  * W_a along face axis e on the left, physical units. */
-static int gks_point(int m, double gamma, double c1, double c2, int tau_mode, double dt, const double *Wl,
+static int gks_point(int m, double gamma, double c1, double c2, int tau_mode, double mu, double dt, const double *Wl,
                      const double *Wr, double dWl[3][5], double dWr[3][5], double *F, double *Ft, double *Wh)
 {
     int nv = m + 2;
@@ -648,7 +654,13 @@ static int gks_point(int m, double gamma, double c1, double c2, int tau_mode, do
      * Euler equations, tau_n for the plain BGK solution */
     double pl = Wl[0] / (2.0 * gl.lam), pr = Wr[0] / (2.0 * gr.lam);
     double tn = c1 * dt + c2 * fabs(pl - pr) / (pl + pr) * dt;
-    double tau = tau_mode ? tn : 0.0;
+    double tau = (tau_mode == 1) ? tn : 0.0;
+    if (tau_mode == 2) {
+        /* Navier-Stokes: the physical collision time from the interface
+         * equilibrium, tau = mu / p0 (Prandtl number 1), enters both */
+        tau = mu / (g0.rho / (2.0 * g0.lam));
+        tn += tau;
+    }
 
     /* the velocity moments the flux and interface state need */
     double e0u[5], eTu[5], eAu[5], fl[5], fr[5], flT[5], frT[5], flA[5], frA[5];
@@ -733,9 +745,19 @@ static void fetch(const or_cfg *c, const double *W, const double *G, int i, int 
     long nc = cells(c);
     long cell = ((long)idx[2] * c->n[1] + idx[1]) * c->n[0] + idx[0];
     for (int v = 0; v < nv; ++v) {
-        w[v] = W[v * nc + cell];
+        /* mirror image: even extension of every variable (transmissive); a
+         * reflective wall also negates the momentum normal to it, so that
+         * component is odd (R8) */
+        double sv = 1.0;
+        if (c->bc == 2)
+            for (int a = 0; a < m; ++a)
+                if (flip[a] && v == 1 + a) sv = -sv;
+        if (c->bc == 3) /* no-slip adiabatic wall: every velocity component is odd */
+            for (int a = 0; a < m; ++a)
+                if (flip[a] && v >= 1 && v <= m) sv = -sv;
+        w[v] = sv * W[v * nc + cell];
         for (int a = 0; a < m; ++a) {
-            double x = G[(a * nv + v) * nc + cell] * c->h;
+            double x = sv * G[(a * nv + v) * nc + cell] * c->h;
             g[a][v] = flip[a] ? -x : x;
         }
     }
@@ -791,7 +813,8 @@ static int check_cfg(const or_cfg *c)
         if (a >= c->dim && c->n[a] != 1) return OR_ERR_ARG;
     }
     if (!(c->h > 0.0) || !(c->gamma > 1.0)) return OR_ERR_ARG;
-    if (c->bc != 0 && c->bc != 1) return OR_ERR_ARG;
+    if (c->bc < 0 || c->bc > 3) return OR_ERR_ARG;
+    if (c->tau_mode == 2 && !(c->mu >= 0.0)) return OR_ERR_ARG;
     if (!(c->adm_delta >= 0.0) || c->adm_delta >= 1.0) return OR_ERR_ARG;
     return OR_OK;
 }
@@ -927,7 +950,7 @@ static int flux_all(const or_cfg *c, double dt, const double *fs, double *out)
                             dW[side][k][fv] = fs[((base + 1 + ax[k]) * ng + gp) * nft + off + f];
                     }
                 double F[5], Ft[5], Wh[5];
-                if (gks_point(m, c->gamma, c->c1_tau, c->c2_tau, c->tau_mode, dt, Wlr[0], Wlr[1], dW[0], dW[1], F, Ft, Wh)) {
+                if (gks_point(m, c->gamma, c->c1_tau, c->c2_tau, c->tau_mode, c->mu, dt, Wlr[0], Wlr[1], dW[0], dW[1], F, Ft, Wh)) {
                     err |= 1; continue;
                 }
                 for (int v = 0; v < nv; ++v) {
@@ -1074,6 +1097,18 @@ double or_max_wavespeed(const or_cfg *c, const double *W)
     return s;
 }
 
+/* max over cells of mu / rho (viscous time step) */
+double or_max_kin_viscosity(const or_cfg *c, const double *W)
+{
+    long nc = cells(c);
+    double s = 0.0;
+    for (long cell = 0; cell < nc; ++cell) {
+        double v = c->mu / W[cell];
+        if (v > s) s = v;
+    }
+    return s;
+}
+
 /* ------------------------------------------------------------------ */
 /* Internals exposed for the pins.                                        */
 /* ------------------------------------------------------------------ */
@@ -1124,14 +1159,14 @@ int or_monomials(int m, int deg, int *e)
 }
 
 /* Flux at one face point in the face frame; dWl/dWr are [m][nv] row-major. */
-int or_gks_point(int m, double gamma, double c1, double c2, int tau_mode, double dt, const double *Wl,
+int or_gks_point(int m, double gamma, double c1, double c2, int tau_mode, double mu, double dt, const double *Wl,
                  const double *Wr, const double *dWl, const double *dWr, double *F, double *Ft, double *Wh)
 {
     double a[3][5], b[3][5];
     int nv = m + 2;
     for (int e = 0; e < m; ++e)
         for (int v = 0; v < nv; ++v) { a[e][v] = dWl[e * nv + v]; b[e][v] = dWr[e * nv + v]; }
-    return gks_point(m, gamma, c1, c2, tau_mode, dt, Wl, Wr, a, b, F, Ft, Wh) ? OR_ERR_NONPHYSICAL : OR_OK;
+    return gks_point(m, gamma, c1, c2, tau_mode, mu, dt, Wl, Wr, a, b, F, Ft, Wh) ? OR_ERR_NONPHYSICAL : OR_OK;
 }
 
 /* Micro-slope solve <a psi> = rhs against the Maxwellian of W (pin P7). */

@@ -17,7 +17,7 @@ from . import _build
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 ST_RHO, ST_P, ST_NAN, ST_FLUX = 1, 2, 4, 8
-BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_NOSLIP = 0, 1, 2, 3
 
 
 class GksError(RuntimeError):
@@ -43,7 +43,20 @@ class Opts(C.Structure):
         ("stream", C.c_void_p),
         ("workspace", C.c_void_p),
         ("workspace_bytes", C.c_size_t),
+        ("mu", C.c_double),
     ]
+
+
+_OPT_CONSTS = ("C", "eps", "C0", "c1_tau", "c2_tau", "adm_delta", "mu")
+
+
+def _set_consts(o: Opts, consts: dict) -> None:
+    """Scheme constants by keyword (an unknown name is an error, not a new
+    Python attribute of the ctypes structure)."""
+    for k, v in consts.items():
+        if k not in _OPT_CONSTS:
+            raise TypeError(f"unknown scheme constant {k!r} (expected one of {_OPT_CONSTS})")
+        setattr(o, k, float(v))
 
 
 _lib = None
@@ -279,8 +292,7 @@ class Batch:
     def __init__(self, nx, ny, hs, gamma=1.4, bc=BC_TRANSMISSIVE, precision=1, stream=None, **consts):
         o = default_opts()
         o.precision = precision
-        for k, v in consts.items():
-            setattr(o, k, v)
+        _set_consts(o, consts)
         sp = _stream_ptr(stream)
         o.stream = sp.value if sp is not None else None
         self.nx, self.ny = list(nx), list(ny)
@@ -324,8 +336,7 @@ class Solver:
         o = default_opts()
         o.precision = precision
         o.limiter = limiter
-        for k, v in consts.items():
-            setattr(o, k, v)
+        _set_consts(o, consts)
         sp = _stream_ptr(stream)
         o.stream = sp.value if sp is not None else None
         self.opts = o

@@ -208,7 +208,8 @@ int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc
     double h = 0.0;
     if (!grid_ok(grid, &h)) return fail(nullptr, GKS_ERR_ARG, "invalid grid (dim 1..3, n >= 1, equal cell size)");
     if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(nullptr, GKS_ERR_ARG, "gamma must be > 1");
-    if (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE) return fail(nullptr, GKS_ERR_ARG, "unknown boundary condition");
+    if (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE && bc != GKS_BC_REFLECTIVE && bc != GKS_BC_NOSLIP)
+        return fail(nullptr, GKS_ERR_ARG, "unknown boundary condition");
     const int want = (grid->dim == 1) ? 8 : 4;
     if (order != want)
         return fail(nullptr, GKS_ERR_UNSUPPORTED, "order %d is not provided in %dD (use %d)", order, grid->dim, want);
@@ -220,6 +221,7 @@ int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc
     if (!(o.C > 0.0) || !(o.eps > 0.0) || !(o.C0 > 0.0) || !(o.c1_tau >= 0.0) || !(o.c2_tau >= 0.0) ||
         !(o.adm_delta >= 0.0) || !(o.adm_delta < 1.0))
         return fail(nullptr, GKS_ERR_ARG, "invalid scheme constants");
+    if (!(o.mu >= 0.0) || !std::isfinite(o.mu)) return fail(nullptr, GKS_ERR_ARG, "viscosity mu must be finite and >= 0");
 
     gks_ctx *c = new (std::nothrow) gks_ctx;
     if (!c) return fail(nullptr, GKS_ERR_OOM, "host allocation");
@@ -308,6 +310,7 @@ int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc
     P.fp.gamma = gamma;
     P.fp.c1 = o.c1_tau;
     P.fp.c2 = o.c2_tau;
+    P.fp.mu = o.mu;
     gks::finalize_kp(P);
 
     cudaError_t e = cudaMemsetAsync(c->ws, 0, L.total, c->stream);

@@ -246,13 +246,15 @@ int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs,
     if (!out) return bfail(nullptr, GKS_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (nbatch < 1 || !nx || !ny || !hs) return bfail(nullptr, GKS_ERR_ARG, "nbatch >= 1 and size arrays required");
-    if (!(gamma > 1.0) || (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE))
+    if (!(gamma > 1.0) || (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE && bc != GKS_BC_REFLECTIVE &&
+                            bc != GKS_BC_NOSLIP))
         return bfail(nullptr, GKS_ERR_ARG, "invalid gamma or boundary condition");
     gks_opts_t o;
     gks_default_opts(&o);
     if (opts) o = *opts;
     if (o.precision != 0 && o.precision != 1) return bfail(nullptr, GKS_ERR_ARG, "precision must be 0 or 1");
     if (o.workspace) return bfail(nullptr, GKS_ERR_UNSUPPORTED, "batched mode allocates its own workspace");
+    if (o.mu != 0.0) return bfail(nullptr, GKS_ERR_UNSUPPORTED, "batched mode solves the Euler equations only (mu = 0)");
     for (int g = 0; g < nbatch; ++g)
         if (nx[g] < 1 || ny[g] < 1 || nx[g] > (1 << 20) || ny[g] > (1 << 20) || !(hs[g] > 0.0))
             return bfail(nullptr, GKS_ERR_ARG, "grid %d: invalid size or cell size", g);

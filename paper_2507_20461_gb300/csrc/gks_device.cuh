@@ -1,5 +1,6 @@
 /*
- * Gas-kinetic interface flux for the Euler equations (device code).
+ * Gas-kinetic interface flux for the Euler and Navier-Stokes equations
+ * (device code).
  *
  * The paper (Sec. 2) takes the flux from the time-dependent gas distribution
  * function of the GKS and defers its formulas to earlier work; this is the
@@ -27,6 +28,16 @@
  *   F  = F0 + (4 ie_h - ie_1)/dt (Fk - F0) + (4 ite_h - ite_1)/dt (FT0 - FTk),
  *   Ft = FA0 + 4 (ie_1 - 2 ie_h)/dt^2 (Fk - F0) + 4 (ite_1 - 2 ite_h)/dt^2 (FT0 - FTk),
  * and the interface state W(dt/2) = W0 + t (1 - e_t) dW0/dt - t e_t WTk.
+ *
+ * Navier-Stokes (Sec. 2, viscous flux of the same scheme; Prandtl number 1):
+ * the general BGK solution with physical collision time tau > 0,
+ *   f(0,t) = (1-e) g0 + ((t+tau) e - tau) T0 g0 + (t - tau + tau e) A0 g0
+ *          + e [ (1 - (t+tau) T_l - tau A_l) H(u) g_l + (same, r) H(-u) g_r ],
+ * tau = mu / p0 and e = exp(-t/(tau_n + tau)); A_l, A_r the time slopes of
+ * the two initial states from their own compatibility conditions.  The tau
+ * terms of the integrals add tau (cF1 D - V) to F, tau cT1 D to Ft and
+ * -tau e_t (WTk + WAk) to W(dt/2), with V = rho0 <u psi (T0 + A0)>_0 and
+ * D = V - FTk - FAk (FAk, WAk: the two half-space moments of A_l, A_r).
  */
 #pragma once
 #include <cuda_runtime.h>
@@ -234,7 +245,8 @@ __device__ __forceinline__ void euler_dflux(const Prim<R, M> &P, const R *W, R g
 struct FluxParams {
     double gamma, c1, c2;
     double gm1, Ntot;      /* gamma - 1, 2 / (gamma - 1) */
-    float fgm1, fNtot, fc1, fc2;
+    double mu;             /* dynamic viscosity (Navier-Stokes flux only) */
+    float fgm1, fNtot, fc1, fc2, fmu;
 };
 
 /* the constant in the precision R */
@@ -255,10 +267,15 @@ inline void fill_flux(FluxParams &fp, double gamma, double c1, double c2)
     fp.fNtot = (float)fp.Ntot;
     fp.fc1 = (float)c1;
     fp.fc2 = (float)c2;
+    fp.fmu = (float)fp.mu;
 }
 
-/* Returns false (and leaves outputs untouched) when a state is not admissible. */
-template <typename R, int M>
+/* Returns false (and leaves outputs untouched) when a state is not admissible.
+ * NS = false: the Euler flux (physical collision time 0 in the Chapman-Enskog
+ * terms).  NS = true: the Navier-Stokes flux with Prandtl number 1, physical
+ * collision time tau = mu / p0 of the interface equilibrium, added to the
+ * numerical one in the relaxation factor. */
+template <typename R, int M, bool NS = false>
 __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *Wl, const R *Wr, const R (*dWl)[M + 2],
                                           const R (*dWr)[M + 2], R *F, R *Ft, R *Wh)
 {
@@ -341,7 +358,52 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
 
     /* collision times and time integrals */
     const R pl = Pl.p, pr = Pr.p;
-    const R tn = pick<R>(fp.c1, fp.fc1) * dt + pick<R>(fp.c2, fp.fc2) * RT<R>::abs_(pl - pr) / (pl + pr) * dt;
+    R tn = pick<R>(fp.c1, fp.fc1) * dt + pick<R>(fp.c2, fp.fc2) * RT<R>::abs_(pl - pr) / (pl + pr) * dt;
+    /* Navier-Stokes only: the time slopes A of the two initial states, each
+     * from its own compatibility condition <psi (sum_e a_e u_e + A) g> = 0,
+     * i.e. the Euler time derivative of that side's state; their half-space
+     * moments carry the physical collision time tau */
+    R tau = R(0), FA[NV], WA[NV];
+    if constexpr (NS) {
+        tau = pick<R>(fp.mu, fp.fmu) / P0.p;
+        tn += tau;
+        R Wlt[NV], Wrt[NV];
+#pragma unroll
+        for (int b = 0; b < NV; ++b) Wlt[b] = Wrt[b] = FA[b] = WA[b] = R(0);
+#pragma unroll
+        for (int e = 0; e < M; ++e) {
+            R d[NV];
+            euler_dflux<R, M>(Pl, Wl, gm1, e, dWl[e], d);
+#pragma unroll
+            for (int b = 0; b < NV; ++b) Wlt[b] -= d[b];
+            euler_dflux<R, M>(Pr, Wr, gm1, e, dWr[e], d);
+#pragma unroll
+            for (int b = 0; b < NV; ++b) Wrt[b] -= d[b];
+        }
+        R Al[NV], Ar[NV];
+        {
+            const R il = R(1) / Pl.rho, ir = R(1) / Pr.rho;
+#pragma unroll
+            for (int b = 0; b < NV; ++b) {
+                Wlt[b] *= il;
+                Wrt[b] *= ir;
+            }
+        }
+        slope<R, M>(Pl, Ntot, Wlt, Al);
+        slope<R, M>(Pr, Ntot, Wrt, Ar);
+        R fl[NV], fr[NV], hl[NV], hr[NV];
+#pragma unroll
+        for (int b = 0; b < NV; ++b) fl[b] = fr[b] = hl[b] = hr[b] = R(0);
+        psi_mom_s<R, M, 1, 0, 0>(Tl, Al, fl);
+        psi_mom_s<R, M, 1, 0, 0>(Tr, Ar, fr);
+        psi_mom_s<R, M, 0, 0, 0>(Tl, Al, hl);
+        psi_mom_s<R, M, 0, 0, 0>(Tr, Ar, hr);
+#pragma unroll
+        for (int b = 0; b < NV; ++b) {
+            FA[b] = Pl.rho * fl[b] + Pr.rho * fr[b];
+            WA[b] = Pl.rho * hl[b] + Pr.rho * hr[b];
+        }
+    }
     const R hdt = R(0.5) * dt;
     R eh = R(0), e1 = R(0);
     if (tn > R(0)) {
@@ -360,6 +422,18 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
         F[b] = F0[b] + cF1 * dk + cF2 * dT;
         Ft[b] = FA0[b] + cT1 * dk + cT2 * dT;
         Wh[b] = W0[b] + hdt * (R(1) - eh) * W0t[b] - hdt * eh * (Pl.rho * WTl[b] + Pr.rho * WTr[b]);
+        if constexpr (NS) {
+            /* the tau terms of the time integrals: with V = <u psi (T0 + A0) g0>
+             * (the equilibrium's viscous part) and D = V - (left + right
+             * half-space <u psi (T + A) g>), F gains tau (cF1 D - V) and Ft
+             * gains tau cT1 D; the interface state gains -tau e (the two
+             * sides' half-space <psi (T + A) g>), since <psi (T0 + A0) g0> = 0 */
+            const R V = P0.rho * FT0[b] + FA0[b];
+            const R D = V - (Pl.rho * FTl[b] + Pr.rho * FTr[b]) - FA[b];
+            F[b] += tau * (cF1 * D - V);
+            Ft[b] += tau * cT1 * D;
+            Wh[b] -= tau * eh * (Pl.rho * WTl[b] + Pr.rho * WTr[b] + WA[b]);
+        }
     }
     return true;
 }

@@ -31,7 +31,7 @@ enum StatusBits : int { ST_RHO = 1, ST_P = 2, ST_NAN = 4, ST_FLUX = 8 };
 
 struct KP {
     int n[3];
-    int bc;      /* 0 periodic, 1 transmissive */
+    int bc;      /* 0 periodic, 1 transmissive, 2 reflective */
     int limiter; /* 0 GENO, 1 linear */
     long ncell;
     long nface[3];
@@ -75,12 +75,23 @@ template <> struct Src<double> {
     const double *W, *G;
     __device__ __forceinline__ double w0(long i) const { return W[i]; }
     __device__ __forceinline__ double delta(long iq, long i0) const { return W[iq] - W[i0]; }
+    /* (sq W[iq]) - (s0 W[i0]) for mirror signs sq, s0 = +-1 */
+    __device__ __forceinline__ double delta_signed(long iq, int sq, long i0, int s0) const
+    {
+        return (sq > 0 ? W[iq] : -W[iq]) - (s0 > 0 ? W[i0] : -W[i0]);
+    }
     __device__ __forceinline__ double grad(long i) const { return G[i]; }
 };
 template <> struct Src<float> {
     const float *hi, *lo, *g;
     __device__ __forceinline__ float w0(long i) const { return hi[i]; }
     __device__ __forceinline__ float delta(long iq, long i0) const { return (hi[iq] - hi[i0]) + (lo[iq] - lo[i0]); }
+    __device__ __forceinline__ float delta_signed(long iq, int sq, long i0, int s0) const
+    {
+        const float hq = sq > 0 ? hi[iq] : -hi[iq], lq = sq > 0 ? lo[iq] : -lo[iq];
+        const float h0 = s0 > 0 ? hi[i0] : -hi[i0], l0 = s0 > 0 ? lo[i0] : -lo[i0];
+        return (hq - h0) + (lq - l0);
+    }
     __device__ __forceinline__ float grad(long i) const { return g[i]; }
 };
 
@@ -106,7 +117,28 @@ __device__ __forceinline__ int map_idx(int i, int n, int bc, int &flip)
     return i;
 }
 
-/* linear cell index and the transmissive sign flips of a (ghost) cell */
+/* Sign of variable v in a mirrored ghost cell: a reflective (slip) wall
+ * negates the momentum component normal to it, a no-slip wall every momentum
+ * component; every other variable (and everything under a transmissive
+ * boundary) is mirrored evenly.  The derivative along axis a
+ * carries this sign times -1 if the ghost is mirrored across axis a. */
+template <int M>
+__device__ __forceinline__ int ghost_sign(const KP &P, const int *flip, int v)
+{
+    int s = 1;
+    if (P.bc == 2) {
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            if (flip[a] && v == 1 + a) s = -s;
+    } else if (P.bc == 3) {
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            if (flip[a] && v >= 1 && v <= M) s = -s;
+    }
+    return s;
+}
+
+/* linear cell index and the mirror flips of a (ghost) cell */
 template <int M>
 __device__ __forceinline__ long cell_lin(const KP &P, int i, int j, int k, int *flip)
 {
@@ -186,8 +218,9 @@ __device__ __forceinline__ void recon1d_face(const KP &P, const double *__restri
         const double sg = flip[0] ? -P.h : P.h;
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-            w[q][v] = W[v * P.ncell + c];
-            d[q][v] = G[v * P.ncell + c] * sg;
+            const double sv = (double)ghost_sign<1>(P, flip, v);
+            w[q][v] = sv * W[v * P.ncell + c];
+            d[q][v] = sv * G[v * P.ncell + c] * sg;
         }
     }
 #pragma unroll
@@ -244,7 +277,7 @@ __device__ __forceinline__ void recon1d_face(const KP &P, const double *__restri
 
 /* FLUX = false: write the interface states face_states[side][v][c][face] (double).
  * FLUX = true : write ff[q][v][face] (R), q = F, dF/dt, W(dt/2). */
-template <typename R, bool FLUX>
+template <typename R, bool FLUX, bool NS = false>
 __global__ void __launch_bounds__(128) face1d_kernel(KP P, const double *__restrict__ W, const double *__restrict__ G,
                                                      const double *__restrict__ dtp, double *__restrict__ fs,
                                                      R *__restrict__ ff, int *__restrict__ status)
@@ -282,7 +315,7 @@ __global__ void __launch_bounds__(128) face1d_kernel(KP P, const double *__restr
     }
     R F[3], Ft[3], Wh[3];
     const R dt = R(dtp[0]);
-    if (!gks_point<R, 1>(P.fp, dt, Wl, Wr, dWl, dWr, F, Ft, Wh)) {
+    if (!gks_point<R, 1, NS>(P.fp, dt, Wl, Wr, dWl, dWr, F, Ft, Wh)) {
         atomicOr(status, ST_FLUX);
 #pragma unroll
         for (int v = 0; v < 3; ++v) F[v] = Ft[v] = Wh[v] = R(0);
@@ -345,19 +378,21 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R
     for (int v = 0; v < NV; ++v) {
         R d[ND];
         const R hr = pick<R>(P.h, P.fh);
+        const int s0v = ghost_sign<M>(P, fl[0], v);
 #pragma unroll
         for (int q = 0; q < 2 * M; ++q) {
-            d[q * (1 + M)] = R(src.delta(v * P.ncell + cl[1 + q], v * P.ncell + cl[0]));
+            const int sq = ghost_sign<M>(P, fl[1 + q], v);
+            d[q * (1 + M)] = R(src.delta_signed(v * P.ncell + cl[1 + q], sq, v * P.ncell + cl[0], s0v));
 #pragma unroll
             for (int a = 0; a < M; ++a) {
                 const R g = src.grad((a * NV + v) * P.ncell + cl[1 + q]) * hr;
-                d[q * (1 + M) + 1 + a] = fl[1 + q][a] ? -g : g;
+                d[q * (1 + M) + 1 + a] = (fl[1 + q][a] ? -sq : sq) < 0 ? -g : g;
             }
         }
 #pragma unroll
         for (int a = 0; a < M; ++a) {
             const R g = src.grad((a * NV + v) * P.ncell + cl[0]) * hr;
-            d[2 * M * (1 + M) + a] = fl[0][a] ? -g : g;
+            d[2 * M * (1 + M) + a] = (fl[0][a] ? -s0v : s0v) < 0 ? -g : g;
         }
         R c[NC];
         Cubic<R, M>::fit(d, c);
@@ -435,7 +470,7 @@ __device__ __forceinline__ long ext_lin(const KP &P, int i, int j, int k)
 /* one (face, Gauss point) of direction D.  FLUX = false writes the states
  * face_states[side][v][c][g][face] (double, global axes); FLUX = true the
  * fluxes ff[q][v][g][face] (R, global momentum order). */
-template <typename R, int M, int D, bool FLUX>
+template <typename R, int M, int D, bool FLUX, bool NS = false>
 __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, const R *__restrict__ B, double dtv,
                                                double *__restrict__ fs, R *__restrict__ ff, int *__restrict__ status,
                                                long t)
@@ -471,7 +506,7 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
             for (int kk = 0; kk < NC; ++kk) c[kk] = B[((long)v * NC + kk) * P.next + ce];
             if (side == 0) CubicEval<R, M, D, 1>::run(g, c, out);
             else CubicEval<R, M, D, 0>::run(g, c, out);
-            const R w0 = R(src.w0(v * P.ncell + cl));
+            const R w0 = R(src.w0(v * P.ncell + cl)) * R(ghost_sign<M>(P, flip, v));
             cw[side][v] = w0;
             st[side][v][0] = w0 + out[0];
 #pragma unroll
@@ -524,7 +559,7 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
     }
     R F[NV], Ft[NV], Wh[NV];
     const R dt = R(dtv);
-    if (!gks_point<R, M>(P.fp, dt, Wl, Wr, dWl, dWr, F, Ft, Wh)) {
+    if (!gks_point<R, M, NS>(P.fp, dt, Wl, Wr, dWl, dWr, F, Ft, Wh)) {
         atomicOr(status, ST_FLUX);
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = Ft[v] = Wh[v] = R(0);
@@ -547,15 +582,16 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
  * spill), measured faster than 127 registers.  (8 blocks, 64 registers, was
  * faster still but moved the FP32 rounding enough to flip a face-state
  * fallback decision against the FP64 oracle on a coarse shock problem.)  The
- * FP64 flux is bound by the FP64 pipe and keeps its registers. */
-template <typename R, int M, int D, bool FLUX>
-__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? 6 : 1)) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
+ * FP64 flux is bound by the FP64 pipe and keeps its registers.  The
+ * Navier-Stokes flux (more live moments) gets 4 blocks per SM in FP32. */
+template <typename R, int M, int D, bool FLUX, bool NS = false>
+__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? (NS ? 4 : 6) : 1)) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
                                                         const double *__restrict__ dtp, double *__restrict__ fs,
                                                         R *__restrict__ ff, int *__restrict__ status)
 {
     constexpr int NG = (M == 2) ? 2 : 4;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < P.nface[D] * NG) face_flux_item<R, M, D, FLUX>(P, src, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
+    if (t < P.nface[D] * NG) face_flux_item<R, M, D, FLUX, NS>(P, src, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
 }
 
 /* ------------------------------------------------------------------ */
@@ -724,7 +760,7 @@ __global__ void shadow_kernel(KP P, const double *__restrict__ W, const double *
 template <int M, typename T>
 __global__ void wavespeed_kernel(KP P, const T *__restrict__ W, unsigned long long *__restrict__ smax)
 {
-    T s = T(0);
+    T s = T(0), ir = T(0); /* max |u_d| + c and max 1 / rho */
     const T gam = pick<T>(P.gamma, (float)(P.fgm1 + 1.0f));
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += (long)gridDim.x * blockDim.x) {
         const T rho = W[c];
@@ -737,26 +773,50 @@ __global__ void wavespeed_kernel(KP P, const T *__restrict__ W, unsigned long lo
         }
         const T p = (gam - T(1)) * (W[(M + 1) * P.ncell + c] - T(0.5) * rho * ke);
         s = fmax(s, um + sqrt(gam * p / rho));
+        ir = fmax(ir, T(1) / rho);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-    __shared__ T red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    for (int o = 16; o > 0; o >>= 1) {
+        s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        ir = fmax(ir, __shfl_xor_sync(0xffffffffu, ir, o));
+    }
+    __shared__ T red[2][32];
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s;
+        red[1][threadIdx.x >> 5] = ir;
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
-        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : T(0);
+        const bool in = threadIdx.x < (blockDim.x >> 5);
+        s = in ? red[0][threadIdx.x] : T(0);
+        ir = in ? red[1][threadIdx.x] : T(0);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+            ir = fmax(ir, __shfl_xor_sync(0xffffffffu, ir, o));
+        }
         /* non-negative doubles order like their bit patterns; NaN is caught on the host */
-        const double sd = (double)s;
-        if (threadIdx.x == 0) atomicMax(smax, (unsigned long long)__double_as_longlong(isnan(sd) ? 1e300 : sd));
+        const double sd = (double)s, id = (double)ir;
+        if (threadIdx.x == 0) {
+            atomicMax(smax, (unsigned long long)__double_as_longlong(isnan(sd) ? 1e300 : sd));
+            atomicMax(smax + 1, (unsigned long long)__double_as_longlong(isnan(id) ? 1e300 : id));
+        }
     }
 }
 
-static __global__ void dt_from_speed_kernel(const unsigned long long *__restrict__ smax, double cfl_h, double *__restrict__ dtp)
+/* dt = cfl h / max(|u_d| + c), and with viscosity mu > 0 also at most
+ * cfl h^2 / (2 (m - 1) nu_max), nu_max = mu max(1 / rho) (Sec. 6; the factor
+ * 2 (m - 1) is taken as 2 in 1D) */
+static __global__ void dt_from_speed_kernel(const unsigned long long *__restrict__ smax, double cfl_h, double visc,
+                                            double *__restrict__ dtp)
 {
-    const double s = __longlong_as_double((long long)*smax);
-    dtp[0] = cfl_h / s;
+    const double s = __longlong_as_double((long long)smax[0]);
+    double dt = cfl_h / s;
+    if (visc > 0.0) {
+        const double nu = visc * __longlong_as_double((long long)smax[1]);
+        dt = fmin(dt, cfl_h / nu);
+    }
+    dtp[0] = dt;
 }
 
 static __global__ void set_scalar_kernel(double *__restrict__ p, double v) { p[0] = v; }

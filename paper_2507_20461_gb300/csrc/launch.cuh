@@ -26,7 +26,8 @@ static cudaError_t flux_impl(gks_ctx *c, int input, double *fs_dev, bool flux)
     if constexpr (M == 1) {
         const unsigned nb = blocks_for(P.n[0] + 1);
         ProfScope ps(c, GKS_KC_FACE);
-        if (flux) face1d_kernel<R, true><<<nb, kBlock, 0, c->stream>>>(P, W, G, c->dt, nullptr, ff, c->status);
+        if (flux && P.fp.mu > 0.0) face1d_kernel<R, true, true><<<nb, kBlock, 0, c->stream>>>(P, W, G, c->dt, nullptr, ff, c->status);
+        else if (flux) face1d_kernel<R, true><<<nb, kBlock, 0, c->stream>>>(P, W, G, c->dt, nullptr, ff, c->status);
         else face1d_kernel<R, false><<<nb, kBlock, 0, c->stream>>>(P, W, G, c->dt, fs_dev, nullptr, c->status);
     } else {
         constexpr int NG = (M == 2) ? 2 : 4;
@@ -41,7 +42,8 @@ static cudaError_t flux_impl(gks_ctx *c, int input, double *fs_dev, bool flux)
             ProfScope ps(c, GKS_KC_FACE);
 #define GKS_FACE(D)                                                                                           \
     if (d == D) {                                                                                             \
-        if (flux) face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+        if (flux && P.fp.mu > 0.0) face_flux_kernel<R, M, D, true, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+        else if (flux) face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
         else face_flux_kernel<R, M, D, false><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, fs_dev, nullptr, c->status); \
     }
             GKS_FACE(0)
@@ -85,7 +87,7 @@ template <int M> cudaError_t launch_update(gks_ctx *c, int stage)
 
 template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl)
 {
-    cudaError_t e = cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), c->stream);
+    cudaError_t e = cudaMemsetAsync(c->smax, 0, 2 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -96,7 +98,12 @@ template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl)
     ProfScope ps(c, GKS_KC_DT);
     if (c->shadows) wavespeed_kernel<M, float><<<nb, 256, 0, c->stream>>>(c->kp, c->s0.hi, c->smax);
     else wavespeed_kernel<M, double><<<nb, 256, 0, c->stream>>>(c->kp, c->W, c->smax);
-    if (cfl > 0.0) dt_from_speed_kernel<<<1, 1, 0, c->stream>>>(c->smax, cfl * c->h, c->dt);
+    if (cfl > 0.0) {
+        /* viscous limit cfl h^2 / (2 (m - 1) nu): passed as the factor
+         * 2 (m - 1) mu / h that turns max(1 / rho) into the rate cfl h / dt */
+        const double visc = c->kp.fp.mu > 0.0 ? 2.0 * (M > 1 ? M - 1 : 1) * c->kp.fp.mu / c->h : 0.0;
+        dt_from_speed_kernel<<<1, 1, 0, c->stream>>>(c->smax, cfl * c->h, visc, c->dt);
+    }
     return cudaGetLastError();
 }
 

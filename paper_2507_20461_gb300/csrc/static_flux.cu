@@ -60,13 +60,14 @@ extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc
     if (nx < 1 || ny < 1 || !(h > 0.0) || !(gamma > 1.0)) return GKS_ERR_ARG;
     /* larger grids do not fit the static scratch */
     if ((long)(nx + 2) * (ny + 2) > kMaxExtCells) return GKS_ERR_ARG;
-    if (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE) return GKS_ERR_ARG;
+    if (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE && bc != GKS_BC_REFLECTIVE && bc != GKS_BC_NOSLIP)
+        return GKS_ERR_ARG;
     if (!W || !G || !face_flux) return GKS_ERR_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return GKS_ERR_ARG;
     gks_opts_t o;
     gks_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != 0) return GKS_ERR_UNSUPPORTED;
+    if (o.precision != 0 || o.mu != 0.0) return GKS_ERR_UNSUPPORTED;
 
     unsigned char *base = nullptr;
     int r = scratch_address(&base);

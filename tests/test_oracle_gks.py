@@ -136,21 +136,26 @@ def _quad_moment(oracle_ignored, W, poly_fn, half):
     return integrate.quad(integrand, lo, hi, epsabs=1e-14, epsrel=1e-13, limit=200)[0]
 
 
-@pytest.mark.parametrize("tau_mode", [1, 0])
+@pytest.mark.parametrize("tau_mode", [1, 0, 2])
 def test_bgk_brute_force_1d(oracle, tau_mode):
     """tau_mode 1: plain BGK solution with one collision time tau_n.
     tau_mode 0 (Euler): the initial state carries no Chapman-Enskog part and
     the equilibrium's Chapman-Enskog terms use the physical tau = 0, which
-    equals the BGK(tau_n) solution plus tau_n (1 - e^{-t/tau_n}) (a0 u + A0) g0."""
+    equals the BGK(tau_n) solution plus tau_n (1 - e^{-t/tau_n}) (a0 u + A0) g0.
+    tau_mode 2 (Navier-Stokes): physical tau_p = mu / p0 in the Chapman-Enskog
+    terms of the initial states and of the equilibrium, relaxation with
+    tau_n = tau_p + c1 dt + ...: the BGK(tau_n) solution whose initial states
+    carry tau_p, plus (tau_n - tau_p) (1 - e^{-t/tau_n}) (a0 u + A0) g0."""
     rng = np.random.default_rng(42)
     dt = 0.05
     c1 = 0.6
+    mu = 0.03 if tau_mode == 2 else 0.0
     for case in range(3):
         Wl = random_state(rng, 1)
         Wr = random_state(rng, 1)
         dWl = rng.normal(size=3) * 0.5
         dWr = rng.normal(size=3) * 0.5
-        F, Ft, Wh = oracle.gks_point(1, GAMMA, dt, Wl, Wr, dWl, dWr, c1=c1, c2=1.0, tau_mode=tau_mode)
+        F, Ft, Wh = oracle.gks_point(1, GAMMA, dt, Wl, Wr, dWl, dWr, c1=c1, c2=1.0, tau_mode=tau_mode, mu=mu)
         rl, Ul, laml, pl = _prim(Wl)
         rr, Ur, lamr, pr = _prim(Wr)
         tau = c1 * dt + abs(pl - pr) / (pl + pr) * dt
@@ -160,7 +165,10 @@ def test_bgk_brute_force_1d(oracle, tau_mode):
             + rr * _quad_moment(None, Wr, lambda u, a=a: _poly_psi(u)[a], -1)
             for a in range(3)
         ])
-        r0, U0, lam0, _ = _prim(W0)
+        r0, U0, lam0, p0 = _prim(W0)
+        tau_p = mu / p0  # physical collision time (tau_mode 2)
+        if tau_mode == 2:
+            tau += tau_p
         # micro-slopes: oracle's slope solve (pinned below by its residual)
         sl = oracle.slope_solve(1, GAMMA, Wl, dWl / rl)
         sr = oracle.slope_solve(1, GAMMA, Wr, dWr / rr)
@@ -207,9 +215,10 @@ def test_bgk_brute_force_1d(oracle, tau_mode):
                 eq[0] += k
                 eq += k * (a0p * (-u * (t - s)) + A0p * s)
             et = math.exp(-t / tau)
-            tau0 = tau if tau_mode == 1 else 0.0  # Chapman-Enskog part of the initial state
-            if tau_mode == 0:
-                eq += tau * (1 - et) * (_mul(a0p, np.stack([u, 0 * u, 0 * u])) + A0p)
+            # collision time of the Chapman-Enskog parts
+            tau0 = {0: 0.0, 1: tau, 2: tau_p}[tau_mode]
+            if tau_mode != 1:
+                eq += (tau - tau0) * (1 - et) * (_mul(a0p, np.stack([u, 0 * u, 0 * u])) + A0p)
             neq = {}
             for key, s_, A_ in (("l", sl, Al), ("r", sr, Ar)):
                 ap = _slope_poly(s_, u)
@@ -332,3 +341,61 @@ def test_mirror_symmetry_of_flux(oracle):
         np.testing.assert_allclose(Fm, sgn * F, rtol=1e-12, atol=1e-13)
         np.testing.assert_allclose(Ftm, sgn * Ft, rtol=1e-10, atol=1e-11)
         np.testing.assert_allclose(Whm, mir(Wh), rtol=1e-12, atol=1e-13)
+
+
+# ------------------------------------------------------------------- P8
+# Navier-Stokes (tau_mode 2, Prandtl number 1): for continuous data the BGK
+# solution is the Chapman-Enskog one, whose flux is the Euler flux plus the
+# Newtonian stress and Fourier heat flux with mu = tau p and conductivity
+# kappa = mu c_p, c_p = gamma / (gamma - 1) (R = 1, T = p / rho).
+
+
+@pytest.mark.parametrize("m", [2, 3])
+def test_ns_shear_stress_closed_form(oracle, m):
+    """Linear shear V(x) = V0 + s x at rest normally (U = 0), uniform rho, p:
+    F = (0, p, -mu s, [0,] -mu s V0) (stress tau_xy = mu dV/dx and its work),
+    for any dt and numerical collision time."""
+    rho, p, V0, s_, mu = 1.3, 0.8, 0.35, 0.7, 0.02
+    W = np.zeros(m + 2)
+    W[0] = rho
+    W[2] = rho * V0
+    W[m + 1] = p / (GAMMA - 1) + 0.5 * rho * V0 * V0
+    dW = np.zeros((m, m + 2))
+    dW[0, 2] = rho * s_
+    dW[0, m + 1] = rho * V0 * s_
+    for dt, c1 in ((0.01, 0.05), (0.2, 0.6)):
+        F, Ft, Wh = oracle.gks_point(m, GAMMA, dt, W, W, dW, dW, c1=c1, tau_mode=2, mu=mu)
+        want = np.zeros(m + 2)
+        want[1] = p
+        want[2] = -mu * s_
+        want[m + 1] = -mu * s_ * V0
+        np.testing.assert_allclose(F, want, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_ns_heat_flux_closed_form(oracle, m):
+    """Fluid at rest at uniform pressure with a density gradient r along the
+    normal: F = (0, p, 0.., -kappa dT/dx) with T = p / rho,
+    dT/dx = -p r / rho^2, kappa = mu gamma / (gamma - 1)."""
+    rho, p, r, mu = 0.9, 1.7, 0.45, 0.015
+    W = np.zeros(m + 2)
+    W[0] = rho
+    W[m + 1] = p / (GAMMA - 1)
+    dW = np.zeros((m, m + 2))
+    dW[0, 0] = r
+    F, Ft, Wh = oracle.gks_point(m, GAMMA, 0.02, W, W, dW, dW, tau_mode=2, mu=mu)
+    want = np.zeros(m + 2)
+    want[1] = p
+    want[m + 1] = mu * GAMMA / (GAMMA - 1) * p * r / rho**2
+    np.testing.assert_allclose(F, want, rtol=1e-12, atol=1e-13)
+
+
+def test_ns_zero_viscosity_is_euler(oracle):
+    rng = np.random.default_rng(7)
+    for m in (1, 2, 3):
+        Wl, Wr = random_state(rng, m), random_state(rng, m)
+        dWl, dWr = rng.normal(size=(m, m + 2)), rng.normal(size=(m, m + 2))
+        a = oracle.gks_point(m, GAMMA, 0.03, Wl, Wr, dWl, dWr, tau_mode=0)
+        b = oracle.gks_point(m, GAMMA, 0.03, Wl, Wr, dWl, dWr, tau_mode=2, mu=0.0)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)

@@ -219,3 +219,75 @@ def test_contact_overshoot_below_linear(oracle):
     lin = _contact_overshoot(oracle, 1)
     assert geno <= 0.5 * lin, (geno, lin)
     assert geno <= 0.03, geno
+
+
+def _mirror_1d(W, G):
+    """Mirror image about the right end: reversed, momentum negated; gradients
+    of even variables negated, of the (odd) momentum kept."""
+    Wm = W[:, ::-1].copy()
+    Wm[1] *= -1
+    Gm = -G[:, :, ::-1].copy()
+    Gm[:, 1] *= -1
+    return Wm, Gm
+
+
+def test_reflective_equals_symmetric_periodic_1d(oracle):
+    """A reflective wall at both ends of [0, 1] is the mirror-symmetric periodic
+    problem on [0, 2] (R8 reading of the reflecting boundaries of Sec. 6.6)."""
+    n = 40
+    W, G, h, _ = I.riemann_1d(n, seed=7)
+    rng = np.random.default_rng(7)
+    W = W * (1 + 0.02 * rng.random(W.shape))
+    W[1] += 0.1
+    G = 0.3 * rng.normal(size=G.shape)
+    Wm, Gm = _mirror_1d(W, G)
+    W2 = np.ascontiguousarray(np.concatenate([W, Wm], axis=1))
+    G2 = np.ascontiguousarray(np.concatenate([G, Gm], axis=2))
+    cfg_r = oracle.make_cfg(1, (n,), h, bc=2)
+    cfg_p = oracle.make_cfg(1, (2 * n,), h, bc=0)
+    dt = 0.3 * h / oracle.max_wavespeed(cfg_p, W2)
+    Wr, Gr = _run(oracle, cfg_r, W, G, dt, 5)
+    Wp, Gp = _run(oracle, cfg_p, W2, G2, dt, 5)
+    np.testing.assert_allclose(Wr, Wp[:, :n], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(Gr, Gp[:, :, :n], rtol=1e-9, atol=1e-9)
+    # the transmissive result differs (the pin is not vacuous)
+    Wt, _ = _run(oracle, oracle.make_cfg(1, (n,), h, bc=1), W, G, dt, 5)
+    assert np.abs(Wt - Wr).max() > 1e-6
+
+
+def test_reflective_equals_symmetric_periodic_2d(oracle):
+    nx, ny = 8, 6
+    W, G, h = I.quadrants_2d(ny, seed=9, nx=nx)
+    rng = np.random.default_rng(9)
+    W = W * (1 + 0.02 * rng.random(W.shape))
+    G = 0.2 * rng.normal(size=G.shape)
+
+    def mirror_x(W, G):
+        Wm = W[:, :, ::-1].copy()
+        Wm[1] *= -1
+        Gm = G[:, :, :, ::-1].copy()
+        Gm[0] *= -1  # d/dx of even variables flips
+        Gm[:, 1] *= -1  # x-momentum is odd
+        return Wm, Gm
+
+    def mirror_y(W, G):
+        Wm = W[:, ::-1, :].copy()
+        Wm[2] *= -1
+        Gm = G[:, :, ::-1, :].copy()
+        Gm[1] *= -1
+        Gm[:, 2] *= -1
+        return Wm, Gm
+
+    Wx, Gx = mirror_x(W, G)
+    Wa = np.concatenate([W, Wx], axis=2)
+    Ga = np.concatenate([G, Gx], axis=3)
+    Wy, Gy = mirror_y(Wa, Ga)
+    W4 = np.ascontiguousarray(np.concatenate([Wa, Wy], axis=1))
+    G4 = np.ascontiguousarray(np.concatenate([Ga, Gy], axis=2))
+    cfg_r = oracle.make_cfg(2, (nx, ny), h, bc=2)
+    cfg_p = oracle.make_cfg(2, (2 * nx, 2 * ny), h, bc=0)
+    dt = 0.3 * h / oracle.max_wavespeed(cfg_p, W4)
+    Wr, Gr = _run(oracle, cfg_r, W, G, dt, 3)
+    Wp, Gp = _run(oracle, cfg_p, W4, G4, dt, 3)
+    np.testing.assert_allclose(Wr, Wp[:, :ny, :nx], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(Gr, Gp[:, :, :ny, :nx], rtol=1e-9, atol=1e-9)
