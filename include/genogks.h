@@ -130,6 +130,15 @@ long gks_face_count(const gks_grid_t *grid);
 int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc, const gks_opts_t *opts,
                     gks_handle_t *out);
 
+/* As geno_gks_create with a boundary condition per side: bc[6] =
+ * {x low, x high, y low, y high, z low, z high} (entries of inactive axes are
+ * ignored).  Periodic must be given on both sides of an axis or on neither
+ * (else GKS_ERR_ARG).  Walls on different sides may differ, e.g. the paper's
+ * viscous shock tube (Sec. 6.9): no-slip on three sides and a slip
+ * (reflective) symmetry line on top. */
+int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const gks_bc_t *bc, const gks_opts_t *opts,
+                          gks_handle_t *out);
+
 /* Copy the state in: W (nv x cells) and G (dim x nv x cells) doubles in the
  * layouts above (host or device memory per on_device).  Clears the status
  * word.  Synchronous with respect to the caller's buffers. */

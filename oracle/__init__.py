@@ -41,6 +41,7 @@ class Cfg(C.Structure):
         ("tau_mode", C.c_int),
         ("adm_delta", C.c_double),
         ("mu", C.c_double),
+        ("bcs", C.c_int * 6),
     ]
 
 
@@ -93,7 +94,12 @@ def make_cfg(dim, n, h, gamma=1.4, bc=0, C_=20.0, eps=1e-15, C0=8.0, c1_tau=0.05
     nn = list(n) + [1] * (3 - len(n))
     if mu > 0.0 and tau_mode == 0:
         tau_mode = 2
-    return Cfg(dim, (C.c_int * 3)(*nn), h, gamma, bc, C_, eps, C0, c1_tau, c2_tau, limiter, tau_mode, adm_delta, mu)
+    # bc: one code for every side, or six (x lo, x hi, y lo, y hi, z lo, z hi)
+    sides = [int(bc)] * 6 if np.isscalar(bc) else [int(b) for b in bc]
+    if len(sides) != 6:
+        raise ValueError("per-side boundary conditions need six entries")
+    return Cfg(dim, (C.c_int * 3)(*nn), h, gamma, sides[0], C_, eps, C0, c1_tau, c2_tau, limiter, tau_mode, adm_delta,
+               mu, (C.c_int * 6)(*sides))
 
 
 def ngauss(dim: int) -> int:

@@ -45,9 +45,14 @@
  *       time-integrated fluxes over dt/2 and dt; the cell-averaged gradients
  *       are refreshed from the interface states at dt/2 of each stage
  *       (Eq. slope, Gauss theorem);
- *   R8  transmissive ghosts are the even extension (normal gradient negated),
+ *   R8  boundary types per side; transmissive ghosts are the even extension
+ *       (normal gradient negated),
  *       reflective ghosts also negate the normal momentum (an odd component),
- *       no-slip walls negate every momentum component,
+ *       no-slip walls negate every momentum component; no wall face
+ *       carries mass or energy flux (walls are at rest and adiabatic; at a
+ *       no-slip wall the mirrored states alone leave a truncation-size mass
+ *       flux through the tangential transport terms, at a slip wall one of
+ *       the size of the rounding asymmetry of the two sides),
  *       periodic ghosts wrap;
  *   R9  a reconstructed interface state whose density or pressure is not
  *       above 0.3 times that of its cell average falls back to the cell
@@ -89,6 +94,8 @@ typedef struct {
                       2: Navier-Stokes, physical tau = mu / p0, tau_n = tau + ... */
     double adm_delta; /* R9 admissibility fraction: 0.3 */
     double mu;     /* dynamic viscosity for tau_mode 2 */
+    int bcs[6];    /* per side (x lo, x hi, y lo, y hi, z lo, z hi), same codes
+                      as bc, which they replace */
 } or_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -728,16 +735,24 @@ static void fetch(const or_cfg *c, const double *W, const double *G, int i, int 
 {
     int m = c->dim, nv = m + 2;
     int idx[3] = {i, j, k};
-    int flip[3] = {0, 0, 0};
+    /* per axis: parity of the mirrors crossed, and of the crossings that
+     * negate the normal momentum (reflective, no-slip) and the tangential
+     * momenta (no-slip) */
+    int mir[3] = {0, 0, 0}, odd_n[3] = {0, 0, 0}, odd_t[3] = {0, 0, 0};
     for (int a = 0; a < m; ++a) {
         int n = c->n[a];
         int x = idx[a];
-        if (c->bc == 0) {
+        int lo = c->bcs[2 * a], hi = c->bcs[2 * a + 1];
+        if (lo == 0) {
             x %= n; if (x < 0) x += n;
         } else {
             while (x < 0 || x >= n) {
-                if (x < 0) { x = -1 - x; flip[a] ^= 1; }
-                if (x >= n) { x = 2 * n - 1 - x; flip[a] ^= 1; }
+                int t;
+                if (x < 0) { x = -1 - x; t = lo; }
+                else { x = 2 * n - 1 - x; t = hi; }
+                mir[a] ^= 1;
+                if (t >= 2) odd_n[a] ^= 1;
+                if (t == 3) odd_t[a] ^= 1;
             }
         }
         idx[a] = x;
@@ -746,19 +761,17 @@ static void fetch(const or_cfg *c, const double *W, const double *G, int i, int 
     long cell = ((long)idx[2] * c->n[1] + idx[1]) * c->n[0] + idx[0];
     for (int v = 0; v < nv; ++v) {
         /* mirror image: even extension of every variable (transmissive); a
-         * reflective wall also negates the momentum normal to it, so that
-         * component is odd (R8) */
+         * reflective wall also negates the momentum normal to it, a no-slip
+         * wall every momentum component (R8) */
         double sv = 1.0;
-        if (c->bc == 2)
-            for (int a = 0; a < m; ++a)
-                if (flip[a] && v == 1 + a) sv = -sv;
-        if (c->bc == 3) /* no-slip adiabatic wall: every velocity component is odd */
-            for (int a = 0; a < m; ++a)
-                if (flip[a] && v >= 1 && v <= m) sv = -sv;
+        for (int a = 0; a < m; ++a) {
+            if (v == 1 + a && odd_n[a]) sv = -sv;
+            if (v >= 1 && v <= m && v != 1 + a && odd_t[a]) sv = -sv;
+        }
         w[v] = sv * W[v * nc + cell];
         for (int a = 0; a < m; ++a) {
             double x = sv * G[(a * nv + v) * nc + cell] * c->h;
-            g[a][v] = flip[a] ? -x : x;
+            g[a][v] = mir[a] ? -x : x;
         }
     }
 }
@@ -813,7 +826,11 @@ static int check_cfg(const or_cfg *c)
         if (a >= c->dim && c->n[a] != 1) return OR_ERR_ARG;
     }
     if (!(c->h > 0.0) || !(c->gamma > 1.0)) return OR_ERR_ARG;
-    if (c->bc < 0 || c->bc > 3) return OR_ERR_ARG;
+    for (int a = 0; a < c->dim; ++a) {
+        int lo = c->bcs[2 * a], hi = c->bcs[2 * a + 1];
+        if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return OR_ERR_ARG;
+        if ((lo == 0) != (hi == 0)) return OR_ERR_ARG; /* periodic pairs */
+    }
     if (c->tau_mode == 2 && !(c->mu >= 0.0)) return OR_ERR_ARG;
     if (!(c->adm_delta >= 0.0) || c->adm_delta >= 1.0) return OR_ERR_ARG;
     return OR_OK;
@@ -952,6 +969,15 @@ static int flux_all(const or_cfg *c, double dt, const double *fs, double *out)
                 double F[5], Ft[5], Wh[5];
                 if (gks_point(m, c->gamma, c->c1_tau, c->c2_tau, c->tau_mode, c->mu, dt, Wlr[0], Wlr[1], dW[0], dW[1], F, Ft, Wh)) {
                     err |= 1; continue;
+                }
+                /* walls (R8), slip or no-slip, at rest and adiabatic: neither
+                 * mass nor energy crosses them; only the momentum flux
+                 * (pressure and stress) is kept */
+                {
+                    long e0 = c->n[0] + (d == 0), e1 = c->n[1] + (d == 1);
+                    long pos = (d == 0) ? f % e0 : (d == 1) ? (f / e0) % e1 : f / (e0 * e1);
+                    int wall = (pos == 0) ? c->bcs[2 * d] : (pos == c->n[d]) ? c->bcs[2 * d + 1] : -1;
+                    if (wall >= 2) F[0] = F[nv - 1] = Ft[0] = Ft[nv - 1] = 0.0;
                 }
                 for (int v = 0; v < nv; ++v) {
                     int fv = v;

@@ -78,6 +78,7 @@ def lib(build: bool = True):
         "gks_workspace_bytes": (C.c_size_t, [gp, C.c_int]),
         "gks_face_count": (C.c_long, [gp]),
         "geno_gks_create": (C.c_int, [gp, C.c_double, C.c_int, C.c_int, op, C.POINTER(vp)]),
+        "geno_gks_create_sides": (C.c_int, [gp, C.c_double, C.c_int, C.POINTER(C.c_int), op, C.POINTER(vp)]),
         "gks_set_state": (C.c_int, [vp, vp, vp, C.c_int]),
         "gks_get_state": (C.c_int, [vp, vp, vp, C.c_int]),
         "geno_reconstruct": (C.c_int, [vp, vp, C.c_int]),
@@ -168,9 +169,18 @@ def workspace_bytes(grid: Grid, precision: int = 0) -> int:
     return int(lib().gks_workspace_bytes(C.byref(grid), precision))
 
 
-def geno_gks_create(grid: Grid, gamma: float, order: int, bc: int, opts: Opts | None = None):
+def geno_gks_create(grid: Grid, gamma: float, order: int, bc, opts: Opts | None = None):
+    """bc: one boundary type for every side, or six (x lo, x hi, y lo, y hi,
+    z lo, z hi) through geno_gks_create_sides."""
     h = C.c_void_p()
-    r = lib().geno_gks_create(C.byref(grid), gamma, order, bc, C.byref(opts) if opts is not None else None, C.byref(h))
+    op = C.byref(opts) if opts is not None else None
+    if isinstance(bc, (int, np.integer)):
+        r = lib().geno_gks_create(C.byref(grid), gamma, order, int(bc), op, C.byref(h))
+    else:
+        sides = [int(b) for b in bc]
+        if len(sides) != 6:
+            raise ValueError("per-side boundary conditions need six entries")
+        r = lib().geno_gks_create_sides(C.byref(grid), gamma, order, (C.c_int * 6)(*sides), op, C.byref(h))
     _check(None, r)
     return h
 

@@ -123,12 +123,12 @@ __global__ void widen_kernel(const float *__restrict__ in, double *__restrict__ 
         out[i] = (double)in[i];
 }
 
-cudaError_t run_flux(gks_ctx *c, int input)
+cudaError_t run_flux(gks_ctx *c, int input, bool sums)
 {
     switch (c->dim) {
-    case 1: return gks::launch_flux<1>(c, input);
-    case 2: return gks::launch_flux<2>(c, input);
-    default: return gks::launch_flux<3>(c, input);
+    case 1: return gks::launch_flux<1>(c, input, sums);
+    case 2: return gks::launch_flux<2>(c, input, sums);
+    default: return gks::launch_flux<3>(c, input, sums);
     }
 }
 
@@ -163,9 +163,10 @@ cudaError_t run_wavespeed(gks_ctx *c, double cfl)
 int two_stages(gks_ctx *c)
 {
     cudaError_t e;
-    if ((e = run_flux(c, 0)) != cudaSuccess) return cuda_fail(c, e, "stage 1 flux");
+    if (c->shadows) c->g_stale = 1;
+    if ((e = run_flux(c, 0, true)) != cudaSuccess) return cuda_fail(c, e, "stage 1 flux");
     if ((e = run_update(c, 1)) != cudaSuccess) return cuda_fail(c, e, "stage 1 update");
-    if ((e = run_flux(c, 1)) != cudaSuccess) return cuda_fail(c, e, "stage 2 flux");
+    if ((e = run_flux(c, 1, true)) != cudaSuccess) return cuda_fail(c, e, "stage 2 flux");
     if ((e = run_update(c, 2)) != cudaSuccess) return cuda_fail(c, e, "stage 2 update");
     return GKS_OK;
 }
@@ -203,13 +204,28 @@ long gks_face_count(const gks_grid_t *grid)
 int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc, const gks_opts_t *opts,
                     gks_handle_t *out)
 {
+    const gks_bc_t sides[6] = {bc, bc, bc, bc, bc, bc};
+    return geno_gks_create_sides(grid, gamma, order, sides, opts, out);
+}
+
+int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const gks_bc_t *bc, const gks_opts_t *opts,
+                          gks_handle_t *out)
+{
     if (!out) return fail(nullptr, GKS_ERR_ARG, "out is NULL");
     *out = nullptr;
     double h = 0.0;
     if (!grid_ok(grid, &h)) return fail(nullptr, GKS_ERR_ARG, "invalid grid (dim 1..3, n >= 1, equal cell size)");
     if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(nullptr, GKS_ERR_ARG, "gamma must be > 1");
-    if (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE && bc != GKS_BC_REFLECTIVE && bc != GKS_BC_NOSLIP)
-        return fail(nullptr, GKS_ERR_ARG, "unknown boundary condition");
+    if (!bc) return fail(nullptr, GKS_ERR_ARG, "boundary conditions are NULL");
+    for (int a = 0; a < grid->dim; ++a) {
+        for (int sd = 0; sd < 2; ++sd) {
+            const gks_bc_t b = bc[2 * a + sd];
+            if (b != GKS_BC_PERIODIC && b != GKS_BC_TRANSMISSIVE && b != GKS_BC_REFLECTIVE && b != GKS_BC_NOSLIP)
+                return fail(nullptr, GKS_ERR_ARG, "unknown boundary condition on side %d", 2 * a + sd);
+        }
+        if ((bc[2 * a] == GKS_BC_PERIODIC) != (bc[2 * a + 1] == GKS_BC_PERIODIC))
+            return fail(nullptr, GKS_ERR_ARG, "axis %d: periodic on one side only", a);
+    }
     const int want = (grid->dim == 1) ? 8 : 4;
     if (order != want)
         return fail(nullptr, GKS_ERR_UNSUPPORTED, "order %d is not provided in %dD (use %d)", order, grid->dim, want);
@@ -297,7 +313,8 @@ int geno_gks_create(const gks_grid_t *grid, double gamma, int order, gks_bc_t bc
         off += f;
     }
     P.nftot = off;
-    P.bc = (int)bc;
+    for (int a = 0; a < 3; ++a)
+        for (int sd = 0; sd < 2; ++sd) P.bcs[a][sd] = (a < grid->dim) ? (int)bc[2 * a + sd] : 0;
     P.limiter = o.limiter;
     P.h = h;
     P.ih = 1.0 / h;
@@ -334,6 +351,7 @@ int gks_set_state(gks_handle_t c, const double *W, const double *G, int on_devic
     cudaError_t e = cudaMemcpyAsync(c->W, W, nW * sizeof(double), k, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->G, G, nG * sizeof(double), k, c->stream);
     if (e == cudaSuccess) e = run_shadow(c);
+    c->g_stale = 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
@@ -347,7 +365,13 @@ int gks_get_state(gks_handle_t c, double *W, double *G, int on_device)
     const size_t nW = (size_t)c->nv * c->kp.ncell, nG = (size_t)c->dim * nW;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaError_t e = cudaSuccess;
-    if (W) e = cudaMemcpyAsync(W, c->W, nW * sizeof(double), k, c->stream);
+    if (G && c->g_stale) {
+        gks::widen_grad_kernel<<<gks::blocks_for((long)nG, 256) > 4096 ? 4096 : gks::blocks_for((long)nG, 256), 256, 0,
+                                 c->stream>>>(c->s0.g, c->G, (long)nG);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) c->g_stale = 0;
+    }
+    if (e == cudaSuccess && W) e = cudaMemcpyAsync(W, c->W, nW * sizeof(double), k, c->stream);
     if (e == cudaSuccess && G) e = cudaMemcpyAsync(G, c->G, nG * sizeof(double), k, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
     const int st = sync_status(c);
@@ -388,7 +412,7 @@ int gks_flux(gks_handle_t c, double dt, double *out, int on_device)
     if (!out) return fail(c, GKS_ERR_ARG, "face_flux is NULL");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GKS_ERR_ARG, "dt must be finite and > 0");
     gks::set_scalar_kernel<<<1, 1, 0, c->stream>>>(c->dt, dt);
-    cudaError_t e = run_flux(c, 0);
+    cudaError_t e = run_flux(c, 0, false);
     if (e != cudaSuccess) return cuda_fail(c, e, "flux");
     const size_t n = c->ff_elems;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

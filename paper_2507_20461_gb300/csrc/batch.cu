@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "batch.h"
@@ -35,6 +36,9 @@ struct gks_batch_ctx {
     int ntiles[gks::BK_COUNT];
     LaunchShape shape[gks::BK_COUNT];
     int tuned;
+    /* mixed precision: per grid, gradients held only in the FP32 shadow
+     * since the last run (G is filled from it when the state is read) */
+    std::vector<char> g_stale;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     double graph_cfl;
@@ -80,7 +84,7 @@ void make_kp(gks::KP &P, int nx, int ny, double h, double gamma, int bc, const g
     P.foff[0] = 0;
     P.foff[1] = P.nface[0];
     P.nftot = P.nface[0] + P.nface[1];
-    P.bc = bc;
+    gks::set_bcs(P, bc);
     P.limiter = o.limiter;
     P.h = h;
     P.ih = 1.0 / h;
@@ -280,6 +284,7 @@ int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs,
     }
     const size_t rs = o.precision ? sizeof(float) : sizeof(double);
     b->hd.resize(nbatch);
+    b->g_stale.assign(nbatch, 0);
     size_t off = al(sizeof(double) * nbatch) + al(sizeof(unsigned long long) * nbatch) + al(256);
     std::vector<size_t> base(nbatch);
     for (int g = 0; g < nbatch; ++g) {
@@ -355,6 +360,7 @@ int gks_batch_set_state(gks_batch_t b, int grid, const double *W, const double *
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.W, W, n * sizeof(double), k, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.G, G, 2 * n * sizeof(double), k, b->stream);
     if (e == cudaSuccess && b->precision == 1) e = gks::batch_shadow(D, b->stream);
+    b->g_stale[grid] = 0;
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     return e == cudaSuccess ? GKS_OK : bcuda(b, e, "batch set_state");
@@ -370,6 +376,10 @@ int gks_batch_get_state(gks_batch_t b, int grid, double *W, double *G, int on_de
     /* the caller's stream may still use the destination buffers */
     cudaError_t e = cudaEventRecord(b->ev_in, b->user_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_in, 0);
+    if (e == cudaSuccess && G && b->precision && b->g_stale[grid]) {
+        e = gks::batch_widen_grad(D, b->stream);
+        if (e == cudaSuccess) b->g_stale[grid] = 0;
+    }
     if (e == cudaSuccess && W) e = cudaMemcpyAsync(W, D.W, n * sizeof(double), k, b->stream);
     if (e == cudaSuccess && G) e = cudaMemcpyAsync(G, D.G, 2 * n * sizeof(double), k, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -385,6 +395,7 @@ int gks_batch_run(gks_batch_t b, double cfl, int nsteps)
 {
     if (!b) return bfail(nullptr, GKS_ERR_ARG, "NULL handle");
     if (!(cfl > 0.0) || !std::isfinite(cfl) || nsteps < 0) return bfail(b, GKS_ERR_ARG, "cfl > 0 and nsteps >= 0 required");
+    if (b->precision == 1 && nsteps > 0) std::fill(b->g_stale.begin(), b->g_stale.end(), 1);
     cudaError_t e = cudaEventRecord(b->ev_in, b->user_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_in, 0);
     if (e != cudaSuccess) return bcuda(b, e, "stream ordering");

@@ -45,6 +45,8 @@ template <typename R> cudaError_t batch_flux(const BatchLaunch &L, const LaunchS
 template <typename R> cudaError_t batch_update(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st);
 cudaError_t batch_dt(const GridDesc *gd, int nb, double cfl, const unsigned long long *smax, double *dt, cudaStream_t st);
 cudaError_t batch_shadow(const GridDesc &g, cudaStream_t st);
+/* FP64 gradients of grid g from its FP32 shadow (mixed precision) */
+cudaError_t batch_widen_grad(const GridDesc &g, cudaStream_t st);
 int batch_occupancy(int kernel, int precision, int block);
 
 } // namespace gks

@@ -21,6 +21,9 @@ struct gks_ctx {
      * of the stage-1 output (s1) that the reconstruction and flux read */
     gks::Shadow s0, s1;
     int shadows;
+    /* mixed precision: the steps keep the gradients in s0.g only; G is
+     * filled from it when the state is read */
+    int g_stale;
     /* device scalars */
     double *dt;
     unsigned long long *smax;
@@ -85,7 +88,9 @@ struct ProfScope {
 /* per-dimension launchers (k1d.cu, k2d.cu, k3d.cu) */
 /* input: 0 = the step's input state (W, G), 1 = the stage-1 output (W*, G*) */
 template <int M> cudaError_t launch_states(gks_ctx *c, int input, double *fs_dev);
-template <int M> cudaError_t launch_flux(gks_ctx *c, int input);
+/* sums: the step path (FP32 multi-D: per-face Gauss sums, read by the update);
+ * false: per-Gauss-point fluxes (gks_flux) */
+template <int M> cudaError_t launch_flux(gks_ctx *c, int input, bool sums);
 template <int M> cudaError_t launch_update(gks_ctx *c, int stage);
 template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl);
 template <int M> cudaError_t launch_shadow(gks_ctx *c);

@@ -79,12 +79,15 @@ __global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? 6 : 1)) bk_
         const GridDesc &g = gd[T.grid];
         const Src<R> src = stage_src_of<R>(g, stage);
         const double dtv = dt[T.grid];
+        /* FP32: per-face Gauss sums, as the single-grid step path (tiles and
+         * blocks hold whole faces: even starts, ends and block sizes) */
+        constexpr bool fsum = sizeof(R) == sizeof(float);
         if (T.kind == 0) {
             for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x)
-                face_flux_item<R, 2, 0, true>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
+                face_flux_item<R, 2, 0, true, false, fsum>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
         } else {
             for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x)
-                face_flux_item<R, 2, 1, true>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
+                face_flux_item<R, 2, 1, true, false, fsum>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
         }
     }
 }
@@ -93,15 +96,22 @@ template <typename R>
 __global__ void __launch_bounds__(256) bk_update(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
                                                  int stage, const double *__restrict__ dt, int *__restrict__ status)
 {
+    __shared__ UpdC uc;
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const Tile T = tiles[ti];
         const GridDesc &g = gd[T.grid];
         const double dtv = dt[T.grid];
+        if constexpr (sizeof(R) == sizeof(float)) {
+            /* the tile's grid's stage constants (the tile loop is uniform over the block) */
+            __syncthreads();
+            if (threadIdx.x == 0) uc = make_updc(dtv, g.P.ih / 2);
+            __syncthreads();
+        }
         for (long c = T.begin + threadIdx.x; c < T.end; c += blockDim.x) {
             if (stage == 1)
-                update_item<R, 2, 1>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status, c);
+                update_item<R, 2, 1>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status, c, uc);
             else
-                update_item<R, 2, 2>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status, c);
+                update_item<R, 2, 2>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status, c, uc);
         }
     }
 }
@@ -130,6 +140,14 @@ cudaError_t batch_shadow(const GridDesc &g, cudaStream_t st)
 {
     const long want = (g.P.ncell + 255) / 256;
     shadow_kernel<2><<<(unsigned)(want < 4096 ? (want > 0 ? want : 1) : 4096), 256, 0, st>>>(g.P, g.W, g.G, g.s0);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_widen_grad(const GridDesc &g, cudaStream_t st)
+{
+    const long n = 2L * 4 * g.P.ncell;
+    const long want = (n + 255) / 256;
+    widen_grad_kernel<<<(unsigned)(want < 4096 ? (want > 0 ? want : 1) : 4096), 256, 0, st>>>(g.s0.g, g.G, n);
     return cudaGetLastError();
 }
 

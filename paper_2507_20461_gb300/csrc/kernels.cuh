@@ -31,7 +31,8 @@ enum StatusBits : int { ST_RHO = 1, ST_P = 2, ST_NAN = 4, ST_FLUX = 8 };
 
 struct KP {
     int n[3];
-    int bc;      /* 0 periodic, 1 transmissive, 2 reflective */
+    int bcs[3][2]; /* per axis, low / high side: 0 periodic (both sides),
+                      1 transmissive, 2 reflective (slip), 3 no-slip wall */
     int limiter; /* 0 GENO, 1 linear */
     long ncell;
     long nface[3];
@@ -45,6 +46,12 @@ struct KP {
     /* FP32 copies for the mixed-precision kernels (fill with finalize_kp) */
     float fh, fih, fgm1, fC, fitanhC, feps, fC0, fadm;
 };
+
+/* the same boundary type on every side */
+inline void set_bcs(KP &P, int bc)
+{
+    for (int a = 0; a < 3; ++a) P.bcs[a][0] = P.bcs[a][1] = bc;
+}
 
 /* derived fields of a parameter block whose double fields are set */
 inline void finalize_kp(KP &P)
@@ -102,17 +109,26 @@ __device__ __forceinline__ void split_store(double w, float *hi, float *lo, long
     lo[i] = (float)(w - (double)a);
 }
 
-__device__ __forceinline__ int map_idx(int i, int n, int bc, int &flip)
+/* Mirror bits of one crossing of a wall of type t (ghost cells are mirror
+ * images): bit 0 the mirror itself (derivatives along the axis change sign),
+ * bit 1 the momentum normal to the wall is odd (reflective and no-slip),
+ * bit 2 the tangential momenta are odd (no-slip). */
+__device__ __forceinline__ int wall_bits(int t) { return t == 1 ? 1 : (t == 2 ? 3 : 7); }
+
+/* index of the (possibly ghost) cell i along an axis of n cells with
+ * boundary types lo / hi; flip accumulates the mirror bits (several
+ * crossings on grids thinner than the stencil) */
+__device__ __forceinline__ int map_idx(int i, int n, int lo, int hi, int &flip)
 {
     if (i >= 0 && i < n) return i;
-    if (bc == 0) {
+    if (lo == 0) {
         i %= n;
         if (i < 0) i += n;
         return i;
     }
     while (i < 0 || i >= n) {
-        if (i < 0) { i = -1 - i; flip ^= 1; }
-        if (i >= n) { i = 2 * n - 1 - i; flip ^= 1; }
+        if (i < 0) { i = -1 - i; flip ^= wall_bits(lo); }
+        if (i >= n) { i = 2 * n - 1 - i; flip ^= wall_bits(hi); }
     }
     return i;
 }
@@ -120,22 +136,37 @@ __device__ __forceinline__ int map_idx(int i, int n, int bc, int &flip)
 /* Sign of variable v in a mirrored ghost cell: a reflective (slip) wall
  * negates the momentum component normal to it, a no-slip wall every momentum
  * component; every other variable (and everything under a transmissive
- * boundary) is mirrored evenly.  The derivative along axis a
- * carries this sign times -1 if the ghost is mirrored across axis a. */
+ * boundary) is mirrored evenly.  The derivative along axis a carries this
+ * sign times -1 if the ghost is mirrored across axis a (flip bit 0). */
 template <int M>
 __device__ __forceinline__ int ghost_sign(const KP &P, const int *flip, int v)
 {
     int s = 1;
-    if (P.bc == 2) {
 #pragma unroll
-        for (int a = 0; a < M; ++a)
-            if (flip[a] && v == 1 + a) s = -s;
-    } else if (P.bc == 3) {
-#pragma unroll
-        for (int a = 0; a < M; ++a)
-            if (flip[a] && v >= 1 && v <= M) s = -s;
+    for (int a = 0; a < M; ++a) {
+        if (v == 1 + a) {
+            if (flip[a] & 2) s = -s;
+        } else if (v >= 1 && v <= M) {
+            if (flip[a] & 4) s = -s;
+        }
     }
     return s;
+}
+
+/* the signs of a (ghost) cell packed in one word: bit v set if variable v
+ * is negated, bit 8 + a set if the cell is mirrored across axis a (its
+ * derivatives along a change sign on top of that) */
+template <int M>
+__device__ __forceinline__ unsigned ghost_mask(const KP &P, const int *flip)
+{
+    unsigned m = 0;
+#pragma unroll
+    for (int v = 0; v < M + 2; ++v)
+        if (ghost_sign<M>(P, flip, v) < 0) m |= 1u << v;
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        if (flip[a] & 1) m |= 1u << (8 + a);
+    return m;
 }
 
 /* linear cell index and the mirror flips of a (ghost) cell */
@@ -143,9 +174,9 @@ template <int M>
 __device__ __forceinline__ long cell_lin(const KP &P, int i, int j, int k, int *flip)
 {
     flip[0] = flip[1] = flip[2] = 0;
-    const int ii = map_idx(i, P.n[0], P.bc, flip[0]);
-    const int jj = (M >= 2) ? map_idx(j, P.n[1], P.bc, flip[1]) : 0;
-    const int kk = (M >= 3) ? map_idx(k, P.n[2], P.bc, flip[2]) : 0;
+    const int ii = map_idx(i, P.n[0], P.bcs[0][0], P.bcs[0][1], flip[0]);
+    const int jj = (M >= 2) ? map_idx(j, P.n[1], P.bcs[1][0], P.bcs[1][1], flip[1]) : 0;
+    const int kk = (M >= 3) ? map_idx(k, P.n[2], P.bcs[2][0], P.bcs[2][1], flip[2]) : 0;
     return ((long)kk * P.n[1] + jj) * P.n[0] + ii;
 }
 
@@ -215,7 +246,7 @@ __device__ __forceinline__ void recon1d_face(const KP &P, const double *__restri
     for (int q = 0; q < 4; ++q) {
         int flip[3];
         const long c = cell_lin<1>(P, f - 2 + q, 0, 0, flip);
-        const double sg = flip[0] ? -P.h : P.h;
+        const double sg = (flip[0] & 1) ? -P.h : P.h;
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
             const double sv = (double)ghost_sign<1>(P, flip, v);
@@ -320,6 +351,8 @@ __global__ void __launch_bounds__(128) face1d_kernel(KP P, const double *__restr
 #pragma unroll
         for (int v = 0; v < 3; ++v) F[v] = Ft[v] = Wh[v] = R(0);
     }
+    /* walls (slip or no-slip) are at rest and adiabatic: neither mass nor energy crosses them */
+    if ((f == 0 && P.bcs[0][0] >= 2) || (f == P.n[0] && P.bcs[0][1] >= 2)) F[0] = F[2] = Ft[0] = Ft[2] = R(0);
     const long nf = P.nftot;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
@@ -364,35 +397,42 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R
     constexpr int NV = M + 2, NC = Cubic<R, M>::NC, ND = Cubic<R, M>::ND;
     int i, j, k;
     if (!ext_cell<M>(P, t, i, j, k)) return;
-    /* the seven (five) cells of the cross: own first, then q = 2 e + (side > 0) */
+    /* the seven (five) cells of the cross: own first, then q = 2 e + (side > 0);
+     * their ghost signs packed one word per cell (ghost_mask) */
     long cl[2 * M + 1];
-    int fl[2 * M + 1][3];
-    cl[0] = cell_lin<M>(P, i, j, k, fl[0]);
+    unsigned sm[2 * M + 1];
+    {
+        int fl[3];
+        cl[0] = cell_lin<M>(P, i, j, k, fl);
+        sm[0] = ghost_mask<M>(P, fl);
 #pragma unroll
-    for (int q = 0; q < 2 * M; ++q) {
-        int o[3] = {i, j, k};
-        o[q / 2] += (q & 1) ? 1 : -1;
-        cl[1 + q] = cell_lin<M>(P, o[0], o[1], o[2], fl[1 + q]);
+        for (int q = 0; q < 2 * M; ++q) {
+            int o[3] = {i, j, k};
+            o[q / 2] += (q & 1) ? 1 : -1;
+            cl[1 + q] = cell_lin<M>(P, o[0], o[1], o[2], fl);
+            sm[1 + q] = ghost_mask<M>(P, fl);
+        }
     }
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) {
         R d[ND];
         const R hr = pick<R>(P.h, P.fh);
-        const int s0v = ghost_sign<M>(P, fl[0], v);
+        const int s0v = ((sm[0] >> v) & 1u) ? -1 : 1;
 #pragma unroll
         for (int q = 0; q < 2 * M; ++q) {
-            const int sq = ghost_sign<M>(P, fl[1 + q], v);
+            const unsigned mq = sm[1 + q];
+            const int sq = ((mq >> v) & 1u) ? -1 : 1;
             d[q * (1 + M)] = R(src.delta_signed(v * P.ncell + cl[1 + q], sq, v * P.ncell + cl[0], s0v));
 #pragma unroll
             for (int a = 0; a < M; ++a) {
                 const R g = src.grad((a * NV + v) * P.ncell + cl[1 + q]) * hr;
-                d[q * (1 + M) + 1 + a] = (fl[1 + q][a] ? -sq : sq) < 0 ? -g : g;
+                d[q * (1 + M) + 1 + a] = (((mq >> v) ^ (mq >> (8 + a))) & 1u) ? -g : g;
             }
         }
 #pragma unroll
         for (int a = 0; a < M; ++a) {
             const R g = src.grad((a * NV + v) * P.ncell + cl[0]) * hr;
-            d[2 * M * (1 + M) + a] = (fl[0][a] ? -s0v : s0v) < 0 ? -g : g;
+            d[2 * M * (1 + M) + a] = (((sm[0] >> v) ^ (sm[0] >> (8 + a))) & 1u) ? -g : g;
         }
         R c[NC];
         Cubic<R, M>::fit(d, c);
@@ -470,7 +510,7 @@ __device__ __forceinline__ long ext_lin(const KP &P, int i, int j, int k)
 /* one (face, Gauss point) of direction D.  FLUX = false writes the states
  * face_states[side][v][c][g][face] (double, global axes); FLUX = true the
  * fluxes ff[q][v][g][face] (R, global momentum order). */
-template <typename R, int M, int D, bool FLUX, bool NS = false>
+template <typename R, int M, int D, bool FLUX, bool NS = false, bool FSUM = false>
 __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, const R *__restrict__ B, double dtv,
                                                double *__restrict__ fs, R *__restrict__ ff, int *__restrict__ status,
                                                long t)
@@ -564,6 +604,42 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = Ft[v] = Wh[v] = R(0);
     }
+    /* walls (slip or no-slip) are at rest and adiabatic: neither mass nor
+     * energy crosses them (exactly, whatever the rounding of the two sides) */
+    if ((idx[D] == 0 && P.bcs[D][0] >= 2) || (idx[D] == P.n[D] && P.bcs[D][1] >= 2))
+        F[0] = F[NV - 1] = Ft[0] = Ft[NV - 1] = R(0);
+    if constexpr (FSUM) {
+        /* step path in FP32: the face's NG Gauss points sit in neighbouring
+         * lanes; sum them there and store one value per face and quantity,
+         * ff[q][v][face] (q = F, dF/dt, W(dt/2)) */
+        static_assert(gfast, "face sums need the Gauss points in neighbouring lanes");
+        const unsigned lane = threadIdx.x & 31u;
+        const unsigned mask = ((1u << NG) - 1u) << (lane & ~(unsigned)(NG - 1));
+#pragma unroll
+        for (int o = 1; o < NG; o <<= 1) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                F[v] += __shfl_xor_sync(mask, F[v], o);
+                Ft[v] += __shfl_xor_sync(mask, Ft[v], o);
+                Wh[v] += __shfl_xor_sync(mask, Wh[v], o);
+            }
+        }
+        if (g == 0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                int fv = v;
+                if (v >= 1 && v <= M) {
+#pragma unroll
+                    for (int kk = 0; kk < M; ++kk)
+                        if (ax[kk] == v - 1) fv = 1 + kk;
+                }
+                ff[(long)(0 * NV + v) * nft + face] = F[fv];
+                ff[(long)(1 * NV + v) * nft + face] = Ft[fv];
+                ff[(long)(2 * NV + v) * nft + face] = Wh[fv];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         int fv = v;
@@ -583,20 +659,96 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
  * faster still but moved the FP32 rounding enough to flip a face-state
  * fallback decision against the FP64 oracle on a coarse shock problem.)  The
  * FP64 flux is bound by the FP64 pipe and keeps its registers.  The
- * Navier-Stokes flux (more live moments) gets 4 blocks per SM in FP32. */
-template <typename R, int M, int D, bool FLUX, bool NS = false>
-__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? (NS ? 4 : 6) : 1)) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
+ * Navier-Stokes flux (more live moments) and the 3D flux (four Gauss points,
+ * five variables) get 4 blocks per SM in FP32. */
+template <typename R, int M, int D, bool FLUX, bool NS = false, bool FSUM = false>
+__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? ((NS || M == 3) ? 4 : 6) : 1)) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
                                                         const double *__restrict__ dtp, double *__restrict__ fs,
                                                         R *__restrict__ ff, int *__restrict__ status)
 {
     constexpr int NG = (M == 2) ? 2 : 4;
+    /* 128 threads and NG | nface * NG: the NG lanes of a face are all in range or all out */
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < P.nface[D] * NG) face_flux_item<R, M, D, FLUX, NS>(P, src, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
+    if (t < P.nface[D] * NG) face_flux_item<R, M, D, FLUX, NS, FSUM>(P, src, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
 }
 
 /* ------------------------------------------------------------------ */
 /* FP64 stage update                                                   */
 /* ------------------------------------------------------------------ */
+/* ------------------------------------------------------------------ */
+/* Double-float arithmetic in FP32 (a value is hi + lo, |lo| <= ulp(hi)/2 */
+/* after normalisation): TwoSum (Knuth), FastTwoSum (Dekker) and TwoProd  */
+/* by fused multiply-add give the rounding errors of FP32 additions and   */
+/* products exactly, so sums and products carry about 48 bits.            */
+/* ------------------------------------------------------------------ */
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 df_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float z = s - a;
+    return F2{s, (a - (s - z)) + (b - z)};
+}
+
+/* requires |a| >= |b| (or a == 0) */
+__device__ __forceinline__ F2 df_fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return F2{s, b - (s - a)};
+}
+
+__device__ __forceinline__ F2 df_mul(F2 k, F2 x)
+{
+    const float p = k.hi * x.hi;
+    float e = fmaf(k.hi, x.hi, -p);
+    e = fmaf(k.hi, x.lo, e);
+    e = fmaf(k.lo, x.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ F2 df_add(F2 a, F2 b)
+{
+    const F2 s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ F2 df_split(double x)
+{
+    const float h = (float)x;
+    return F2{h, (float)(x - (double)h)};
+}
+
+/* the stage constants of the mixed-precision update as double-floats:
+ * with S the exact face sum of a cell and cw = 1 / (h NG),
+ *   stage 1: W* - W = k0 S(F) + k1 S(Ft),  Acc = k2 S(F) + k3 S(Ft);
+ *   stage 2: W^{n+1} - W = Acc + k4 S(Ft*) */
+struct UpdC {
+    F2 k[5];
+};
+
+__device__ __forceinline__ UpdC make_updc(double dt, double cw)
+{
+    UpdC u;
+    u.k[0] = df_split(-0.5 * dt * cw);
+    u.k[1] = df_split(-0.125 * dt * dt * cw);
+    u.k[2] = df_split(-dt * cw);
+    u.k[3] = df_split(-dt * dt / 6.0 * cw);
+    u.k[4] = df_split(-dt * dt / 3.0 * cw);
+    return u;
+}
+
+/* s + e += x exactly up to the rounding of e (Knuth's TwoSum, FP32 adds
+ * only, so nothing can be contracted or reassociated) */
+__device__ __forceinline__ void two_sum_acc(float &s, float &e, float x)
+{
+    const float t = s + x;
+    const float z = t - s;
+    e += (s - (t - z)) + (x - z);
+    s = t;
+}
+
 template <int M>
 __device__ __forceinline__ long face_of(const KP &P, int d, int i, int j, int k, int s)
 {
@@ -613,64 +765,79 @@ template <typename R, int M, int STAGE>
 __device__ __forceinline__ void update_item(const KP &P, const R *__restrict__ ff, double dt, double *__restrict__ W,
                                             double *__restrict__ G, double *__restrict__ Ws, double *__restrict__ Gs,
                                             double *__restrict__ Acc, const Shadow &s0, const Shadow &s1,
-                                            int *__restrict__ status, long cell)
+                                            int *__restrict__ status, long cell, const UpdC &uc)
 {
     constexpr int NV = M + 2, NG = (M == 1) ? 1 : ((M == 2) ? 2 : 4);
     if constexpr (sizeof(R) == sizeof(float) && M >= 2) {
-        /* mixed precision: face sums in FP32 (the face values are FP32), the
-         * stage combination of the averages in FP64, the next stage's input
-         * as the FP32 shadow (s1 after stage 1, s0 after stage 2) */
+        /* mixed precision: the face values are per-face FP32 sums over the
+         * Gauss points (ff[q][v][face]).  A cell adds its faces' fluxes
+         * exactly (double-float accumulation), so each face's flux leaves one
+         * cell and enters the other without a rounding of its own, and the
+         * stage combination runs in double-float FP32 arithmetic (about 48
+         * bits; GB300's FP64 rate is 1/64 of FP32).  Stage 1 writes the next
+         * input directly as its FP32 shadow s1 (= s0 + increment) and keeps
+         * Acc as a float pair; stage 2 adds its increment to the FP64 state
+         * W and re-splits W into s0, so the shadow never drifts from W.  The
+         * sums of the averages are conserved to FP64 rounding.  Gradients
+         * (not conserved) come from FP32 differences and live in the shadow
+         * only; the FP64 G is filled from it when the state is read. */
         const int i = (int)(cell % P.n[0]);
         const int j = (int)((cell / P.n[0]) % P.n[1]);
         const int k = (M >= 3) ? (int)(cell / ((long)P.n[0] * P.n[1])) : 0;
-        const long nft = P.nftot;
-        const float wg = 1.0f / NG, ihf = P.fih;
+        const long nft = P.nftot, nc = P.ncell;
+        const float gw = P.fih / NG;
         long fp[M], fm[M];
 #pragma unroll
         for (int d = 0; d < M; ++d) {
             fp[d] = face_of<M>(P, d, i, j, k, 1);
             fm[d] = face_of<M>(P, d, i, j, k, 0);
         }
+        float *acc = (float *)Acc; /* [2][nv][cell]: hi, lo */
         const Shadow &so = (STAGE == 1) ? s1 : s0;
-        double Wn[NV];
+        float wn[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            float DF = 0.f, DFt = 0.f;
+            const float *f0 = ff + (long)(0 * NV + v) * nft, *f1 = ff + (long)(1 * NV + v) * nft,
+                        *f2 = ff + (long)(2 * NV + v) * nft;
+            float sF = 0.f, eF = 0.f, sT = 0.f, eT = 0.f;
 #pragma unroll
             for (int d = 0; d < M; ++d) {
-                float Dh = 0.f;
-#pragma unroll
-                for (int g = 0; g < NG; ++g) {
-                    const long o0 = ((long)(0 * NV + v) * NG + g) * nft, o1 = ((long)(1 * NV + v) * NG + g) * nft,
-                               o2 = ((long)(2 * NV + v) * NG + g) * nft;
-                    DF += (float)ff[o0 + fp[d]] - (float)ff[o0 + fm[d]];
-                    DFt += (float)ff[o1 + fp[d]] - (float)ff[o1 + fm[d]];
-                    Dh += (float)ff[o2 + fp[d]] - (float)ff[o2 + fm[d]];
+                if (STAGE == 1) {
+                    two_sum_acc(sF, eF, f0[fp[d]]);
+                    two_sum_acc(sF, eF, -f0[fm[d]]);
                 }
-                const float gv = Dh * wg * ihf;
-                so.g[(d * NV + v) * P.ncell + cell] = gv;
-                if (STAGE == 2) G[(d * NV + v) * P.ncell + cell] = (double)gv;
+                two_sum_acc(sT, eT, f1[fp[d]]);
+                two_sum_acc(sT, eT, -f1[fm[d]]);
+                so.g[(d * NV + v) * nc + cell] = (f2[fp[d]] - f2[fm[d]]) * gw;
             }
-            const double dF = (double)(DF * wg * ihf), dFt = (double)(DFt * wg * ihf);
-            double w;
+            const F2 ST{sT, eT};
             if (STAGE == 1) {
-                w = W[v * P.ncell + cell] - 0.5 * dt * dF - dt * dt * 0.125 * dFt;
-                Acc[v * P.ncell + cell] = -dt * dF - dt * dt / 6.0 * dFt;
+                const F2 SF{sF, eF};
+                const F2 dW = df_add(df_mul(uc.k[0], SF), df_mul(uc.k[1], ST));
+                const F2 A = df_add(df_mul(uc.k[2], SF), df_mul(uc.k[3], ST));
+                acc[v * nc + cell] = A.hi;
+                acc[(NV + v) * nc + cell] = A.lo;
+                const F2 w = df_add(F2{s0.hi[v * nc + cell], s0.lo[v * nc + cell]}, dW);
+                so.hi[v * nc + cell] = w.hi;
+                so.lo[v * nc + cell] = w.lo;
+                wn[v] = w.hi;
             } else {
-                w = W[v * P.ncell + cell] + Acc[v * P.ncell + cell] - dt * dt / 3.0 * dFt;
-                W[v * P.ncell + cell] = w;
+                const F2 dW = df_add(F2{acc[v * nc + cell], acc[(NV + v) * nc + cell]}, df_mul(uc.k[4], ST));
+                const double w = (W[v * nc + cell] + (double)dW.hi) + (double)dW.lo;
+                W[v * nc + cell] = w;
+                split_store(w, so.hi, so.lo, v * nc + cell);
+                wn[v] = (float)w;
             }
-            split_store(w, so.hi, so.lo, v * P.ncell + cell);
-            Wn[v] = w;
         }
-        double ke = 0.0;
+        /* admissibility flags from the FP32 values of the new state */
+        float ke = 0.f;
 #pragma unroll
-        for (int a = 0; a < M; ++a) ke += Wn[1 + a] * Wn[1 + a];
-        const double p = (P.gamma - 1.0) * (Wn[M + 1] - 0.5 * ke / Wn[0]);
+        for (int a = 0; a < M; ++a) ke += wn[1 + a] * wn[1 + a];
+        const float p = P.fgm1 * (wn[M + 1] - 0.5f * ke / wn[0]);
         int st = 0;
-        if (!(Wn[0] > 0.0)) st |= ST_RHO;
-        if (!(p > 0.0)) st |= ST_P;
-        if (!isfinite(p) || !isfinite(Wn[0])) st |= ST_NAN;
+        if (!(wn[0] > 0.f)) st |= ST_RHO;
+        if (!(p > 0.f)) st |= ST_P;
+        if (!isfinite(p) || !isfinite(wn[0])) st |= ST_NAN;
         if (st) atomicOr(status, st);
         return;
     }
@@ -733,8 +900,22 @@ __global__ void __launch_bounds__(256) update_kernel(KP P, const R *__restrict__
                                                     double *__restrict__ Acc, Shadow s0, Shadow s1,
                                                     int *__restrict__ status)
 {
+    /* the mixed-precision stage constants, once per block */
+    __shared__ UpdC uc;
+    if constexpr (sizeof(R) == sizeof(float) && M >= 2) {
+        if (threadIdx.x == 0) uc = make_updc(dtp[0], P.ih / ((M == 2) ? 2 : 4));
+        __syncthreads();
+    }
     const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell < P.ncell) update_item<R, M, STAGE>(P, ff, dtp[0], W, G, Ws, Gs, Acc, s0, s1, status, cell);
+    if (cell < P.ncell) update_item<R, M, STAGE>(P, ff, dtp[0], W, G, Ws, Gs, Acc, s0, s1, status, cell, uc);
+}
+
+/* FP64 gradients from the FP32 shadow (mixed precision keeps the gradients
+ * in the shadow only; this fills G when the state is read) */
+static __global__ void widen_grad_kernel(const float *__restrict__ g, double *__restrict__ G, long n)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        G[i] = (double)g[i];
 }
 
 /* FP32 shadow of the FP64 state (after the state is set) */

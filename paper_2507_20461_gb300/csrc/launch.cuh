@@ -16,8 +16,11 @@ template <> inline Src<float> stage_src<float>(gks_ctx *c, int input)
     return Src<float>{s.hi, s.lo, s.g};
 }
 
+/* flux = false: interface states into fs_dev; flux = true: fluxes per Gauss
+ * point into c->ff, or (sums, FP32 multi-D step path) per-face sums over the
+ * Gauss points */
 template <typename R, int M>
-static cudaError_t flux_impl(gks_ctx *c, int input, double *fs_dev, bool flux)
+static cudaError_t flux_impl(gks_ctx *c, int input, double *fs_dev, bool flux, bool sums = false)
 {
     const KP &P = c->kp;
     R *ff = (R *)c->ff;
@@ -42,9 +45,17 @@ static cudaError_t flux_impl(gks_ctx *c, int input, double *fs_dev, bool flux)
             ProfScope ps(c, GKS_KC_FACE);
 #define GKS_FACE(D)                                                                                           \
     if (d == D) {                                                                                             \
-        if (flux && P.fp.mu > 0.0) face_flux_kernel<R, M, D, true, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
-        else if (flux) face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
-        else face_flux_kernel<R, M, D, false><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, fs_dev, nullptr, c->status); \
+        if constexpr (sizeof(R) == sizeof(float)) {                                                           \
+            if (flux && sums && P.fp.mu > 0.0)                                                                \
+                face_flux_kernel<R, M, D, true, true, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+            else if (flux && sums)                                                                            \
+                face_flux_kernel<R, M, D, true, false, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+        }                                                                                                     \
+        if (flux && !(sizeof(R) == sizeof(float) && sums)) {                                                 \
+            if (P.fp.mu > 0.0) face_flux_kernel<R, M, D, true, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+            else face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+        }                                                                                                     \
+        if (!flux) face_flux_kernel<R, M, D, false><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, fs_dev, nullptr, c->status); \
     }
             GKS_FACE(0)
             GKS_FACE(1)
@@ -60,9 +71,10 @@ template <int M> cudaError_t launch_states(gks_ctx *c, int input, double *fs_dev
     return c->precision ? flux_impl<float, M>(c, input, fs_dev, false) : flux_impl<double, M>(c, input, fs_dev, false);
 }
 
-template <int M> cudaError_t launch_flux(gks_ctx *c, int input)
+template <int M> cudaError_t launch_flux(gks_ctx *c, int input, bool sums)
 {
-    return c->precision ? flux_impl<float, M>(c, input, nullptr, true) : flux_impl<double, M>(c, input, nullptr, true);
+    return c->precision ? flux_impl<float, M>(c, input, nullptr, true, sums)
+                        : flux_impl<double, M>(c, input, nullptr, true, sums);
 }
 
 template <typename R, int M> static cudaError_t update_impl(gks_ctx *c, int stage)
@@ -118,7 +130,7 @@ template <int M> cudaError_t launch_shadow(gks_ctx *c)
 
 #define GKS_INSTANTIATE(M)                                                                                \
     template cudaError_t launch_states<M>(gks_ctx *, int, double *);                                      \
-    template cudaError_t launch_flux<M>(gks_ctx *, int);                                                  \
+    template cudaError_t launch_flux<M>(gks_ctx *, int, bool);                                            \
     template cudaError_t launch_update<M>(gks_ctx *, int);                                                \
     template cudaError_t launch_wavespeed<M>(gks_ctx *, double);                                          \
     template cudaError_t launch_shadow<M>(gks_ctx *);

@@ -91,7 +91,7 @@ extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc
     P.nface[1] = (long)nx * (ny + 1);
     P.foff[1] = P.nface[0];
     P.nftot = P.nface[0] + P.nface[1];
-    P.bc = (int)bc;
+    gks::set_bcs(P, (int)bc);
     P.limiter = o.limiter;
     P.h = h;
     P.ih = 1.0 / h;

@@ -5,7 +5,9 @@ cell-averaged gradients ``G`` of initial conditions shaped like the paper's
 test families (Sec. 6): advected density sine waves (Sec. 6.1, Sec. 6.10),
 two-state Riemann problems (Sec. 6.5), four-quadrant Riemann problems, smooth
 density modes crossed by planar shocks (shock/smooth-wave interaction,
-Sec. 6.3) and a solenoidal turbulence-like velocity field (Sec. 6.13).
+Sec. 6.3), a solenoidal turbulence-like velocity field (Sec. 6.13), and the
+two viscous cases: the viscous shock tube (Sec. 6.9) and the Taylor-Green
+vortex.
 Both the CUDA library's tests and the oracle's tests take their inputs here.
 
 Layouts: ``W[v][k][j][i]`` with v = rho, rho u (, rho v, rho w), rho E;
@@ -219,3 +221,59 @@ def turbulence_3d(n: int, seed: int, gamma: float = GAMMA, mach: float = 0.6, k0
             G[d, 1 + a] = dvel[a][d]
         G[d, 4] = sum(vel[a] * dvel[a][d] for a in range(3))
     return W, G, 1.0 / n
+
+
+def viscous_shock_tube(nx: int, gamma: float = GAMMA):
+    """Viscous shock tube (Sec. 6.9) on [0, 1] x [0, 0.5]: (rho, u, v, p) =
+    (120, 0, 0, 120/gamma) for x < 0.5 and (1.2, 0, 0, 1.2/gamma) beyond;
+    nx x nx/2 cells (nx even, so the jump lies on a face), zero gradients.
+    The paper's walls: no-slip at x = 0, 1 and y = 0, a symmetry line at
+    y = 0.5 (boundary sides (3, 3, 3, 2)); mu = 0.005 (Re = 200), Pr = 1."""
+    if nx % 2:
+        raise ValueError("nx must be even")
+    ny = nx // 2
+    h = 1.0 / nx
+    x = (np.arange(nx) + 0.5) * h
+    rho1 = np.where(x < 0.5, 120.0, 1.2)
+    rho = np.repeat(rho1[None, :], ny, axis=0)
+    p = rho / gamma
+    W = _cons(rho, [np.zeros_like(rho), np.zeros_like(rho)], p, gamma)
+    G = np.zeros((2, 4, ny, nx))
+    return W, G, h
+
+
+def taylor_green_3d(n: int, gamma: float = GAMMA, mach: float = 0.1, u0: float = 1.0):
+    """Taylor-Green vortex on the periodic cube [-pi, pi]^3 (n^3 cells):
+    u = u0 sin x cos y cos z, v = -u0 cos x sin y cos z, w = 0, uniform
+    temperature, rho = 1 + (gamma mach^2 / 16)(cos 2x + cos 2y)(cos 2z + 2),
+    p = rho / (gamma mach^2) (so that mach = u0 / sqrt(gamma p0 / rho0)).
+    Averages are the point values at cell centres and gradients the exact
+    derivatives there (synthetic input).  Returns W, G, h = 2 pi / n."""
+    h = 2 * math.pi / n
+    c = -math.pi + (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    sx, cx, sy, cy, sz, cz = np.sin(X), np.cos(X), np.sin(Y), np.cos(Y), np.sin(Z), np.cos(Z)
+    u = u0 * sx * cy * cz
+    v = -u0 * cx * sy * cz
+    w = np.zeros_like(u)
+    a = gamma * mach * mach / 16.0
+    rho = 1.0 + a * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+    T = 1.0 / (gamma * mach * mach)
+    p = rho * T
+    W = _cons(rho, [u, v, w], p, gamma)
+    # exact derivatives: d/dx, d/dy, d/dz of rho, u, v (w = 0)
+    drho = [
+        -2 * a * np.sin(2 * X) * (np.cos(2 * Z) + 2.0),
+        -2 * a * np.sin(2 * Y) * (np.cos(2 * Z) + 2.0),
+        -2 * a * (np.cos(2 * X) + np.cos(2 * Y)) * np.sin(2 * Z),
+    ]
+    du = [u0 * cx * cy * cz, -u0 * sx * sy * cz, -u0 * sx * cy * sz]
+    dv = [u0 * sx * sy * cz, -u0 * cx * cy * cz, u0 * cx * sy * sz]
+    G = np.zeros((3, 5, n, n, n))
+    for d in range(3):
+        G[d, 0] = drho[d]
+        G[d, 1] = drho[d] * u + rho * du[d]
+        G[d, 2] = drho[d] * v + rho * dv[d]
+        # E = p / (gamma - 1) + rho |u|^2 / 2 with p = rho T
+        G[d, 4] = drho[d] * T / (gamma - 1) + 0.5 * drho[d] * (u * u + v * v) + rho * (u * du[d] + v * dv[d])
+    return W, G, h

@@ -142,3 +142,68 @@ def test_ns_shear_wave_decay(precision):
     want = amp * math.exp(-mu * k * k * nsteps * dt)
     assert abs(got / want - 1) <= 5e-4, (got, want)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_taylor_green_decay(precision):
+    """Taylor-Green vortex on 32^3 cells, Re = 100 (L0 = 2 pi), t = 0.1:
+    E_k(t) / E_k(0) = exp(-6 nu t) (single Stokes mode, energy-conserving
+    inviscid dynamics), through gks_step_cfl."""
+    from paper_2507_20461_gb300 import inputs as I
+
+    n, mu, cfl = 32, 2 * math.pi / 100, 0.4
+    W, G, h = I.taylor_green_3d(n)
+    cfg = O.make_cfg(3, (n, n, n), h, bc=0, mu=mu)
+    dt = O.cfl_dt(cfg, W, cfl)
+    nsteps = 10
+    s = B.Solver((n, n, n), lo=[-math.pi] * 3, hi=[math.pi] * 3, bc=B.BC_PERIODIC, precision=precision, mu=mu)
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    for _ in range(nsteps):
+        s.step(dt)
+    s.get_state(Wd, Gd)
+    Wn = Wd.cpu().numpy()
+
+    def ek(W):
+        return float(np.mean(0.5 * (W[1] ** 2 + W[2] ** 2 + W[3] ** 2) / W[0]))
+
+    ratio = ek(Wn) / ek(W)
+    want = math.exp(-6 * mu * nsteps * dt)
+    assert abs(ratio / want - 1) <= 3e-4, (ratio, want)
+    s.close()
+
+
+def test_viscous_shock_tube():
+    """Viscous shock tube (Sec. 6.9), 80 x 40 cells, no-slip walls on three
+    sides and a slip symmetry line on top, mu = 0.005: ten FP64 steps match the
+    oracle step by step; FP64 and mixed runs of 80 CFL steps stay admissible
+    and conserve mass (closed box)."""
+    from paper_2507_20461_gb300 import inputs as I
+
+    nx, mu = 80, 0.005
+    sides = (3, 3, 3, 2, 0, 0)
+    W, G, h = I.viscous_shock_tube(nx)
+    n = (nx, nx // 2)
+    cfg = O.make_cfg(2, n, h, bc=sides, mu=mu)
+    s = B.Solver(n, lo=[0, 0], hi=[1.0, 0.5], bc=sides, precision=0, mu=mu)
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    Wo, Go = W.copy(), G.copy()
+    for _ in range(10):
+        dt = O.cfl_dt(cfg, Wo, 0.4)
+        assert O.step(cfg, dt, Wo, Go) == 0
+        s.step(dt)
+    s.get_state(Wd, Gd)
+    assert _rel_l1(Wd.cpu().numpy(), Wo).max() <= 1e-11
+    s.close()
+    mass0 = W[0].sum()
+    for precision in (0, 1):
+        s = B.Solver(n, lo=[0, 0], hi=[1.0, 0.5], bc=sides, precision=precision, mu=mu)
+        Wd, Gd = _dev(W), _dev(G)
+        s.set_state(Wd, Gd)
+        s.step_cfl(0.4, 80)
+        s.get_state(Wd, Gd)
+        rho = Wd.cpu().numpy()[0]
+        assert np.isfinite(rho).all() and rho.min() > 0
+        assert abs(rho.sum() / mass0 - 1) <= 1e-12
+        s.close()

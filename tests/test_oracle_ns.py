@@ -174,3 +174,30 @@ def test_viscous_time_step(oracle):
         smax = (np.abs(vel).max(axis=0) + np.sqrt(GAMMA * p / rho)).max()
         want = min(0.4 * h / smax, 0.4 * h * h / (2 * max(dim - 1, 1) * mu / rho.min()))
         assert oracle.cfl_dt(cfg, W, 0.4) == pytest.approx(want, rel=1e-13)
+
+
+def test_taylor_green_initial_decay(oracle):
+    """Taylor-Green vortex (u0 = 1, Ma 0.1): the initial field is a single
+    Stokes mode with |k|^2 = 3 per component and the inviscid dynamics keeps
+    the kinetic energy, so E_k(t) / E_k(0) = exp(-6 nu t) up to O(nu t^3) and
+    the Mach-number effects; 12^3 cells, Re = 100 with L0 = 2 pi (mu = 0.0628)."""
+    from paper_2507_20461_gb300 import inputs as I
+
+    n, mu, t_end = 12, 2 * math.pi / 100, 0.06
+    W, G, h = I.taylor_green_3d(n)
+    cfg = oracle.make_cfg(3, (n, n, n), h, bc=0, mu=mu)
+
+    def ek(W):
+        return float(np.mean(0.5 * (W[1] ** 2 + W[2] ** 2 + W[3] ** 2) / W[0]))
+
+    E0 = ek(W)
+    assert E0 == pytest.approx(0.125, rel=2e-3)  # <|u|^2 / 2> = 1/8 (cell-centre sampling)
+    t = 0.0
+    while t < t_end - 1e-14:
+        dt = min(oracle.cfl_dt(cfg, W, 0.4), t_end - t)
+        assert oracle.step(cfg, dt, W, G) == 0
+        t += dt
+    ratio = ek(W) / E0
+    want = math.exp(-6 * mu * t_end)
+    # the decay is 2.2 %; a viscosity off by 10 % would miss by 2e-3
+    assert abs(ratio / want - 1) <= 1e-3, (ratio, want)

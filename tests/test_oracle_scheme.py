@@ -291,3 +291,102 @@ def test_reflective_equals_symmetric_periodic_2d(oracle):
     Wp, Gp = _run(oracle, cfg_p, W4, G4, dt, 3)
     np.testing.assert_allclose(Wr, Wp[:, :ny, :nx], rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(Gr, Gp[:, :, :ny, :nx], rtol=1e-9, atol=1e-9)
+
+
+def _y_uniform_channel_state(nx, ny, seed):
+    """y-independent state with nonzero normal and tangential velocity near the
+    x-walls (averages and x-gradients; no y-gradients)."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / nx
+    x = (np.arange(nx) + 0.5) * h
+    rho = 1.0 + 0.2 * np.sin(3 * x) + 0.02 * rng.random(nx)
+    u = 0.1 * np.cos(2 * x) + 0.01 * rng.random(nx)
+    v = 0.3 * np.sin(5 * x) + 0.01 * rng.random(nx)
+    p = 1.0 + 0.1 * np.cos(4 * x)
+    W1 = np.stack([rho, rho * u, rho * v, p / 0.4 + 0.5 * rho * (u * u + v * v)])
+    G1 = 0.3 * rng.normal(size=(4, nx))
+    W = np.ascontiguousarray(np.repeat(W1[:, None, :], ny, axis=1))
+    G = np.zeros((2, 4, ny, nx))
+    G[0] = np.repeat(G1[:, None, :], ny, axis=1)
+    return W, G, h
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.01])
+def test_noslip_walls_equal_point_symmetric_periodic(oracle, mu):
+    """No-slip walls at x = 0, 1 (y periodic) for a y-independent state are the
+    periodic problem on [0, 2] with the point-symmetric extension
+    (x -> -x, u -> -u, v -> -v), a symmetry of the equations for such states;
+    per-side boundary conditions (R8), Euler and Navier-Stokes."""
+    nx, ny = 12, 3
+    W, G, h = _y_uniform_channel_state(nx, ny, 11)
+    Wm = W[:, :, ::-1].copy()
+    Wm[1:3] *= -1
+    Gm = G[:, :, :, ::-1].copy()
+    Gm[0] *= -1
+    Gm[:, 1:3] *= -1
+    W2 = np.ascontiguousarray(np.concatenate([W, Wm], axis=2))
+    G2 = np.ascontiguousarray(np.concatenate([G, Gm], axis=3))
+    cfg_w = oracle.make_cfg(2, (nx, ny), h, bc=(3, 3, 0, 0, 0, 0), mu=mu)
+    cfg_p = oracle.make_cfg(2, (2 * nx, ny), h, bc=0, mu=mu)
+    dt = 0.3 * h / oracle.max_wavespeed(cfg_p, W2)
+    Ww, Gw = _run(oracle, cfg_w, W, G, dt, 4)
+    Wp, Gp = _run(oracle, cfg_p, W2, G2, dt, 4)
+    np.testing.assert_allclose(Ww, Wp[:, :, :nx], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(Gw, Gp[:, :, :, :nx], rtol=1e-9, atol=1e-9)
+    # a slip wall gives another result (the tangential momentum is even there)
+    Ws, _ = _run(oracle, oracle.make_cfg(2, (nx, ny), h, bc=(2, 2, 0, 0, 0, 0), mu=mu), W, G, dt, 4)
+    assert np.abs(Ws - Ww).max() > 1e-6
+
+
+def test_noslip_channel_mode_decay(oracle):
+    """Shear mode v = a sin(pi x) between no-slip walls at x = 0, 1 decays as
+    exp(-nu pi^2 t) (linearised Navier-Stokes, Sec. 6.9's wall condition)."""
+    nx, ny, mu, amp, p0, t_end = 32, 2, 0.01, 1e-3, 100.0, 0.5
+    h = 1.0 / nx
+    x = (np.arange(nx) + 0.5) * h
+    k = np.pi
+    s_avg = (np.cos(k * (x - h / 2)) - np.cos(k * (x + h / 2))) / (k * h)
+    c_avg = (np.sin(k * (x + h / 2)) - np.sin(k * (x - h / 2))) / (k * h)
+    v = amp * s_avg
+    W = np.zeros((4, ny, nx))
+    G = np.zeros((2, 4, ny, nx))
+    W[0], W[2], W[3] = 1.0, v, p0 / 0.4 + 0.5 * v * v
+    G[0, 2] = amp * k * c_avg
+    G[0, 3] = v * amp * k * c_avg
+    cfg = oracle.make_cfg(2, (nx, ny), h, bc=(3, 3, 0, 0, 0, 0), mu=mu)
+    t = 0.0
+    while t < t_end - 1e-14:
+        dt = min(oracle.cfl_dt(cfg, W, 0.4), t_end - t)
+        assert oracle.step(cfg, dt, W, G) == 0
+        t += dt
+    got = 2 * np.mean((W[2] / W[0]).mean(axis=0) * np.sin(k * x)) / (np.sin(k * h / 2) / (k * h / 2))
+    want = amp * np.exp(-mu * k * k * t_end)
+    assert abs(got / want - 1) <= 2e-4, (got, want)
+
+
+def test_per_side_bc_plumbing(oracle):
+    n = (10, 8)
+    W, G, h = I.quadrants_2d(8, seed=3, nx=10)
+    dt = 0.3 * h / oracle.max_wavespeed(oracle.make_cfg(2, n, h, bc=1), W)
+    a, _ = _run(oracle, oracle.make_cfg(2, n, h, bc=1), W, G, dt, 2)
+    b, _ = _run(oracle, oracle.make_cfg(2, n, h, bc=(1, 1, 1, 1, 0, 0)), W, G, dt, 2)
+    np.testing.assert_array_equal(a, b)
+    # periodic on one side only is rejected
+    bad = oracle.make_cfg(2, n, h, bc=(0, 1, 1, 1, 0, 0))
+    assert oracle.step(bad, dt, W.copy(), G.copy()) != 0
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.005])
+def test_closed_box_conserves_mass_and_energy(oracle, mu):
+    """Viscous shock tube box (Sec. 6.9): no-slip walls on three sides, a slip
+    symmetry line on top.  Nothing but momentum crosses a wall, so the summed
+    mass and energy stay fixed to rounding (R8: a no-slip wall face carries no
+    mass or energy flux)."""
+    nx = 24
+    W, G, h = I.viscous_shock_tube(nx)
+    cfg = oracle.make_cfg(2, (nx, nx // 2), h, bc=(3, 3, 3, 2, 0, 0), mu=mu)
+    m0, e0 = W[0].sum(), W[3].sum()
+    for _ in range(8):
+        assert oracle.step(cfg, oracle.cfl_dt(cfg, W, 0.4), W, G) == 0
+    assert abs(W[0].sum() / m0 - 1) <= 1e-14
+    assert abs(W[3].sum() / e0 - 1) <= 1e-14
