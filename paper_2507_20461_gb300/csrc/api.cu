@@ -313,6 +313,14 @@ int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const
         off += f;
     }
     P.nftot = off;
+    /* the kernels decompose indices in 32-bit arithmetic */
+    bool fits = next < (1L << 32) && ncell < (1L << 32);
+    for (int d = 0; d < grid->dim; ++d) fits = fits && P.nface[d] * gks::ngauss(grid->dim) < (1L << 32);
+    if (!fits) {
+        if (c->own_ws) cudaFree(c->ws);
+        delete c;
+        return fail(nullptr, GKS_ERR_UNSUPPORTED, "grid too large (an index space reaches 2^32)");
+    }
     for (int a = 0; a < 3; ++a)
         for (int sd = 0; sd < 2; ++sd) P.bcs[a][sd] = (a < grid->dim) ? (int)bc[2 * a + sd] : 0;
     P.limiter = o.limiter;

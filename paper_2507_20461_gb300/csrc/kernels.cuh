@@ -29,6 +29,36 @@ namespace gks {
 
 enum StatusBits : int { ST_RHO = 1, ST_P = 2, ST_NAN = 4, ST_FLUX = 8 };
 
+/* Division of 32-bit unsigned integers by a divisor fixed at launch:
+ * q = floor(n / d) = floor(M n / 2^64) with M = ceil(2^64 / d), exact for all
+ * n, d < 2^32 (Lemire, Kaser and Kurz, "Faster remainder by direct
+ * computation", 2019, Theorem 1); M = 0 marks d = 1.  Replaces the 64-bit
+ * divisions of the index decompositions (a long instruction sequence each). */
+struct FDiv {
+    unsigned d;
+    unsigned long long M;
+};
+
+inline FDiv make_fdiv(unsigned d)
+{
+    FDiv f;
+    f.d = d;
+    f.M = (d <= 1) ? 0ull : (~0ull / d + 1ull);
+    return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(const FDiv &f, unsigned n)
+{
+    return f.M ? (unsigned)__umul64hi(f.M, (unsigned long long)n) : n;
+}
+
+/* q = n / d, returns n % d */
+__device__ __forceinline__ unsigned fdivmod(const FDiv &f, unsigned n, unsigned &q)
+{
+    q = fdiv(f, n);
+    return n - q * f.d;
+}
+
 struct KP {
     int n[3];
     int bcs[3][2]; /* per axis, low / high side: 0 periodic (both sides),
@@ -45,6 +75,10 @@ struct KP {
     FluxParams fp;
     /* FP32 copies for the mixed-precision kernels (fill with finalize_kp) */
     float fh, fih, fgm1, fC, fitanhC, feps, fC0, fadm;
+    /* index decompositions (fill with finalize_kp; every index space of a
+     * launch is below 2^32): cells per axis, extended box, per face
+     * direction its two leading extents and its face count */
+    FDiv dn[3], dext[2], dface[3][2], dnf[3];
 };
 
 /* the same boundary type on every side */
@@ -64,6 +98,14 @@ inline void finalize_kp(KP &P)
     P.fitanhC = (float)P.itanhC;
     P.feps = (float)P.eps;
     P.fC0 = (float)P.C0;
+    for (int a = 0; a < 3; ++a) P.dn[a] = make_fdiv((unsigned)P.n[a]);
+    P.dext[0] = make_fdiv((unsigned)P.ext[0]);
+    P.dext[1] = make_fdiv((unsigned)P.ext[1]);
+    for (int d = 0; d < 3; ++d) {
+        P.dface[d][0] = make_fdiv((unsigned)(P.n[0] + (d == 0)));
+        P.dface[d][1] = make_fdiv((unsigned)(P.n[1] + (d == 1)));
+        P.dnf[d] = make_fdiv((unsigned)(P.nface[d] > 0 ? P.nface[d] : 1));
+    }
     P.fadm = (float)P.adm;
 }
 
@@ -382,9 +424,10 @@ template <typename R> struct Cubic<R, 3> {
 template <int M>
 __device__ __forceinline__ bool ext_cell(const KP &P, long t, int &i, int &j, int &k)
 {
-    i = (int)(t % P.ext[0]) - 1;
-    j = (M >= 2) ? (int)((t / P.ext[0]) % P.ext[1]) - 1 : 0;
-    k = (M >= 3) ? (int)(t / ((long)P.ext[0] * P.ext[1])) - 1 : 0;
+    unsigned q0, q1;
+    i = (int)fdivmod(P.dext[0], (unsigned)t, q0) - 1;
+    j = (M >= 2) ? (int)fdivmod(P.dext[1], q0, q1) - 1 : 0;
+    k = (M >= 3) ? (int)q1 - 1 : 0;
     int out = (i < 0 || i >= P.n[0]);
     if (M >= 2) out += (j < 0 || j >= P.n[1]);
     if (M >= 3) out += (k < 0 || k >= P.n[2]);
@@ -522,13 +565,14 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
      * point per warp, so the per-point evaluation does not diverge in this
      * compute-bound kernel. */
     constexpr bool gfast = sizeof(R) == sizeof(float);
-    const int g = gfast ? (int)(t % NG) : (int)(t / nf);
-    const long fl = gfast ? t / NG : t - (long)g * nf;
-    int e0 = P.n[0] + (D == 0), e1 = P.n[1] + (D == 1);
+    const unsigned tu = (unsigned)t;
+    const int g = gfast ? (int)(tu % NG) : (int)fdiv(P.dnf[D], tu);
+    const long fl = gfast ? (long)(tu / NG) : t - (long)g * nf;
     int idx[3];
-    idx[0] = (int)(fl % e0);
-    idx[1] = (M >= 2) ? (int)((fl / e0) % e1) : 0;
-    idx[2] = (M >= 3) ? (int)(fl / ((long)e0 * e1)) : 0;
+    unsigned q0, q1;
+    idx[0] = (int)fdivmod(P.dface[D][0], (unsigned)fl, q0);
+    idx[1] = (M >= 2) ? (int)fdivmod(P.dface[D][1], q0, q1) : 0;
+    idx[2] = (M >= 3) ? (int)q1 : 0;
     const R gm1 = pick<R>(P.fp.gm1, P.fgm1);
     /* interface states, global axes: st[side][v][c], c = 0 value, 1 + e d/dx_e */
     R st[2][NV][M + 1], cw[2][NV];
@@ -781,9 +825,10 @@ __device__ __forceinline__ void update_item(const KP &P, const R *__restrict__ f
          * sums of the averages are conserved to FP64 rounding.  Gradients
          * (not conserved) come from FP32 differences and live in the shadow
          * only; the FP64 G is filled from it when the state is read. */
-        const int i = (int)(cell % P.n[0]);
-        const int j = (int)((cell / P.n[0]) % P.n[1]);
-        const int k = (M >= 3) ? (int)(cell / ((long)P.n[0] * P.n[1])) : 0;
+        unsigned q0, q1;
+        const int i = (int)fdivmod(P.dn[0], (unsigned)cell, q0);
+        const int j = (int)fdivmod(P.dn[1], q0, q1);
+        const int k = (M >= 3) ? (int)q1 : 0;
         const long nft = P.nftot, nc = P.ncell;
         const float gw = P.fih / NG;
         long fp[M], fm[M];
@@ -841,9 +886,10 @@ __device__ __forceinline__ void update_item(const KP &P, const R *__restrict__ f
         if (st) atomicOr(status, st);
         return;
     }
-    const int i = (int)(cell % P.n[0]);
-    const int j = (M >= 2) ? (int)((cell / P.n[0]) % P.n[1]) : 0;
-    const int k = (M >= 3) ? (int)(cell / ((long)P.n[0] * P.n[1])) : 0;
+    unsigned q0, q1 = 0;
+    const int i = (int)fdivmod(P.dn[0], (unsigned)cell, q0);
+    const int j = (M >= 2) ? (int)fdivmod(P.dn[1], q0, q1) : 0;
+    const int k = (M >= 3) ? (int)q1 : 0;
     const double ih = P.ih, wg = 1.0 / NG;
     const long nft = P.nftot;
     long fp[M], fm[M];

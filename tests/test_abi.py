@@ -78,3 +78,22 @@ def test_null_handles_are_rejected():
     assert L.gks_status(None) == B.ERR_ARG
     assert L.gks_destroy(None) == B.OK
     assert L.gks_batch_run(None, 0.4, 1) == B.ERR_ARG
+
+
+def test_fast_division_formula():
+    """The kernels divide 32-bit indices by launch-fixed divisors as
+    floor(M n / 2^64) with M = ceil(2^64 / d) (Lemire, Kaser and Kurz 2019,
+    Theorem 1); the host computes M as floor((2^64 - 1) / d) + 1.  Exact for
+    every n, d < 2^32 (checked here on edges and random samples)."""
+    import random
+
+    rng = random.Random(5)
+    ds = [2, 3, 5, 7, 10, 64, 1000, 2049, 2050, 4097, 65535, 65536, 2**31 - 1, 2**31, 2**32 - 1]
+    ds += [rng.randrange(2, 2**32) for _ in range(300)]
+    for d in ds:
+        M = (2**64 - 1) // d + 1
+        ns = [0, 1, d - 1, d, d + 1, 2**32 - 1, (2**32 - 1) // d * d, (2**32 - 1) // d * d - 1]
+        ns += [rng.randrange(0, 2**32) for _ in range(200)]
+        for n in ns:
+            if 0 <= n < 2**32:
+                assert (M * n) >> 64 == n // d, (d, n)
