@@ -87,7 +87,12 @@ typedef enum {
 typedef struct {
     int precision;    /* 0: FP64 throughout; 1: reconstruction and flux in FP32,
                          averages, gradients and stage combination in FP64       */
-    int limiter;      /* 0: GENO; 1: linear scheme (chi = 1)                     */
+    int limiter;      /* 0: GENO; 1: linear scheme (chi = 1); 2: WENO-Z weights
+                         (Eq. wgt-WENO-Z); 3: TENO weights (Eq. wgt-TENO-1,
+                         Eq. wgt-TENO-2).  2 and 3 use GENO's candidates (the
+                         high-order polynomial and the sub-stencil polynomials)
+                         in the adaptive-order combination
+                         (w0/d0) q^H + sum_k (w_k - (w0/d0) d_k) p_k           */
     double C;         /* path-function steepness, Eq. HLP-weight (20)            */
     double eps;       /* regulariser of the indicators, Eq. HLP-sp (1e-15)       */
     double C0;        /* weight of the central 1D sub-stencil, Sec. 3.3 (8)      */
@@ -104,6 +109,10 @@ typedef struct {
                          Sec. 6.9): physical collision time mu / p in the BGK
                          solution, added to tau_n, and the viscous time-step
                          limit in gks_step_cfl (0)                               */
+    double ao_d0;     /* limiters 2, 3: linear weight d0 of the high-order
+                         candidate; the sub-stencils share 1 - d0 (0.85)         */
+    double teno_ct;   /* limiter 3: cut-off C_T (1e-6; the paper uses 1e-3 for
+                         the Titarev-Toro problem), Sec. 5.1                     */
 } gks_opts_t;
 
 typedef struct gks_ctx *gks_handle_t;

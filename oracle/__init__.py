@@ -42,6 +42,8 @@ class Cfg(C.Structure):
         ("adm_delta", C.c_double),
         ("mu", C.c_double),
         ("bcs", C.c_int * 6),
+        ("ao_d0", C.c_double),
+        ("teno_ct", C.c_double),
     ]
 
 
@@ -90,7 +92,7 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def make_cfg(dim, n, h, gamma=1.4, bc=0, C_=20.0, eps=1e-15, C0=8.0, c1_tau=0.05, c2_tau=1.0, limiter=0, tau_mode=0, adm_delta=0.3, mu=0.0) -> Cfg:
+def make_cfg(dim, n, h, gamma=1.4, bc=0, C_=20.0, eps=1e-15, C0=8.0, c1_tau=0.05, c2_tau=1.0, limiter=0, tau_mode=0, adm_delta=0.3, mu=0.0, ao_d0=0.85, teno_ct=1e-6) -> Cfg:
     nn = list(n) + [1] * (3 - len(n))
     if mu > 0.0 and tau_mode == 0:
         tau_mode = 2
@@ -99,7 +101,7 @@ def make_cfg(dim, n, h, gamma=1.4, bc=0, C_=20.0, eps=1e-15, C0=8.0, c1_tau=0.05
     if len(sides) != 6:
         raise ValueError("per-side boundary conditions need six entries")
     return Cfg(dim, (C.c_int * 3)(*nn), h, gamma, sides[0], C_, eps, C0, c1_tau, c2_tau, limiter, tau_mode, adm_delta,
-               mu, (C.c_int * 6)(*sides))
+               mu, (C.c_int * 6)(*sides), ao_d0, teno_ct)
 
 
 def ngauss(dim: int) -> int:

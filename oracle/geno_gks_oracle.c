@@ -54,6 +54,12 @@
  *       flux through the tangential transport terms, at a slip wall one of
  *       the size of the rounding asymmetry of the two sides),
  *       periodic ghosts wrap;
+ *   R14 WENO-Z / TENO variants (Sec. 5.1): the same candidates as GENO (the
+ *       high-order polynomial with indicator IS^H, and the sub-stencil
+ *       polynomials) in the adaptive-order combination
+ *       (w0/d0) q^H + sum_k (w_k - (w0/d0) d_k) p_k with d0 = 0.85 and the
+ *       sub-stencils sharing 1 - d0 as GENO's low-order weights do;
+ *       tau_Z = IS^tau;
  *   R9  a reconstructed interface state whose density or pressure is not
  *       above 0.3 times that of its cell average falls back to the cell
  *       average with zero slopes.
@@ -89,13 +95,15 @@ typedef struct {
     double C0;     /* central sub-stencil weight, Sec. 3.3: 8 */
     double c1_tau; /* R6 */
     double c2_tau; /* R6 */
-    int limiter;   /* 0 GENO, 1 linear (chi = 1) */
+    int limiter;   /* 0 GENO, 1 linear (chi = 1), 2 WENO-Z, 3 TENO (R14) */
     int tau_mode;  /* 0: Euler (physical tau = 0); 1: tau = tau_n (plain BGK);
                       2: Navier-Stokes, physical tau = mu / p0, tau_n = tau + ... */
     double adm_delta; /* R9 admissibility fraction: 0.3 */
     double mu;     /* dynamic viscosity for tau_mode 2 */
     int bcs[6];    /* per side (x lo, x hi, y lo, y hi, z lo, z hi), same codes
                       as bc, which they replace */
+    double ao_d0;  /* R14: linear weight of the high-order candidate: 0.85 */
+    double teno_ct; /* TENO cut-off C_T (Sec. 5.1): 1e-6 */
 } or_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -318,6 +326,26 @@ static long double geno_chi(long double ISt, long double ISH, long double ISL, i
     return tanhl(C * alpha) / tanhl(C);
 }
 
+/* WENO-Z weights (Eq. wgt-WENO-Z) or TENO weights (Eq. wgt-TENO-1 with the
+ * exponent 7, Eq. wgt-TENO-2 with the cut-off C_T) over the candidates
+ * k = 0 (the high-order polynomial, indicator IS^H) and k = 1..K (the
+ * sub-stencil polynomials), linear weights d[0..K], tau_Z = IS^tau (R14).
+ * Returns the normalised nonlinear weights w[0..K]. */
+static void ao_weights(int limiter, int K, const long double *d, const long double *IS, long double tau,
+                       long double eps, long double ct, long double *w)
+{
+    long double wt[8], s = 0.0L;
+    if (limiter == 2) {
+        for (int k = 0; k <= K; ++k) wt[k] = d[k] * (1.0L + tau / (IS[k] + eps));
+    } else {
+        long double g[8], gs = 0.0L;
+        for (int k = 0; k <= K; ++k) { g[k] = powl(1.0L / (IS[k] + eps), 7); gs += g[k]; }
+        for (int k = 0; k <= K; ++k) wt[k] = (g[k] / gs <= ct) ? 0.0L : d[k];
+    }
+    for (int k = 0; k <= K; ++k) s += wt[k];
+    for (int k = 0; k <= K; ++k) w[k] = wt[k] / s;
+}
+
 /* ------------------------------------------------------------------ */
 /* 1D eighth-order compact GENO reconstruction (Sec. 4.2).               */
 /* Reconstruction cell at offset 0 in the arrays w[-2..2], d[-2..2]       */
@@ -380,6 +408,18 @@ static int geno1d(const double *w5, const double *d5, int side, const or_cfg *cf
     for (int j = 0; j < 3; ++j) { qL += wt[j] / ws * pv[j]; qLd += wt[j] / ws * pd[j]; }
     o->val = (double)(chi * pH + (1.0L - chi) * qL); /* Eq. 8th-compact-HLP */
     o->der = (double)(chi * pHd + (1.0L - chi) * qLd);
+    if (cfg->limiter >= 2) {
+        /* R14: R = (w0/d0) p^7 + sum_k (w_k - (w0/d0) d_k) p_k, the sub-stencils
+         * sharing 1 - d0 in GENO's low-order proportions (1, C0, 1) */
+        long double d0 = cfg->ao_d0, dd[4] = {d0, 0, 0, 0}, I4[4] = {ISH, IS[0], IS[1], IS[2]}, w[4];
+        for (int j = 0; j < 3; ++j) dd[j + 1] = (1.0L - d0) * d[j] / (cfg->C0 + 2.0L);
+        ao_weights(cfg->limiter, 3, dd, I4, ISt, eps, cfg->teno_ct, w);
+        chi = w[0] / d0;
+        long double v = chi * pH, dv = chi * pHd;
+        for (int j = 0; j < 3; ++j) { v += (w[j + 1] - chi * dd[j + 1]) * pv[j]; dv += (w[j + 1] - chi * dd[j + 1]) * pd[j]; }
+        o->val = (double)v;
+        o->der = (double)dv;
+    }
     o->chi = (double)chi;
     for (int j = 0; j < 3; ++j) o->IS[j] = (double)IS[j];
     o->ISH = (double)ISH; o->ISL = (double)ISL; o->ISt = (double)ISt;
@@ -441,8 +481,21 @@ static int genomd(int m, double W0, const double *D0, const double *Wn, const do
     /* blended polynomial in the cubic's monomial basis; the linear
      * monomials come first after the constant (monset ordering by degree) */
     for (int k = 0; k < s3.nmon; ++k) o->coef[k] = chi * c3[k];
-    for (int q = 0; q < k0; ++q)
-        for (int k = 0; k < s1.nmon; ++k) o->coef[k] += (1.0L - chi) * wt[q] / ws * c1[q][k];
+    if (cfg->limiter >= 2) {
+        /* R14: (w0/d0) p^3 + sum_q (w_q - (w0/d0) d_q) p_q, the 2m linear
+         * polynomials sharing 1 - d0 equally */
+        long double d0 = cfg->ao_d0, dd[7], I7[7], w[7];
+        dd[0] = d0; I7[0] = ISH;
+        for (int q = 0; q < k0; ++q) { dd[q + 1] = (1.0L - d0) / k0; I7[q + 1] = IS[q]; }
+        ao_weights(cfg->limiter, k0, dd, I7, ISt, eps, cfg->teno_ct, w);
+        chi = w[0] / d0;
+        for (int k = 0; k < s3.nmon; ++k) o->coef[k] = chi * c3[k];
+        for (int q = 0; q < k0; ++q)
+            for (int k = 0; k < s1.nmon; ++k) o->coef[k] += (w[q + 1] - chi * dd[q + 1]) * c1[q][k];
+    } else {
+        for (int q = 0; q < k0; ++q)
+            for (int k = 0; k < s1.nmon; ++k) o->coef[k] += (1.0L - chi) * wt[q] / ws * c1[q][k];
+    }
     o->chi = (double)chi; o->ISH = (double)ISH; o->ISL = (double)ISL; o->ISt = (double)ISt;
     for (int q = 0; q < k0; ++q) o->IS[q] = (double)IS[q];
     return 0;
@@ -833,6 +886,9 @@ static int check_cfg(const or_cfg *c)
     }
     if (c->tau_mode == 2 && !(c->mu >= 0.0)) return OR_ERR_ARG;
     if (!(c->adm_delta >= 0.0) || c->adm_delta >= 1.0) return OR_ERR_ARG;
+    if (c->limiter < 0 || c->limiter > 3) return OR_ERR_ARG;
+    if (c->limiter >= 2 && (!(c->ao_d0 > 0.0) || !(c->ao_d0 < 1.0) || !(c->teno_ct > 0.0) || !(c->teno_ct < 1.0)))
+        return OR_ERR_ARG;
     return OR_OK;
 }
 

@@ -18,6 +18,7 @@ OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 ST_RHO, ST_P, ST_NAN, ST_FLUX = 1, 2, 4, 8
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_NOSLIP = 0, 1, 2, 3
+LIMITER_GENO, LIMITER_LINEAR, LIMITER_WENOZ, LIMITER_TENO = 0, 1, 2, 3
 
 
 class GksError(RuntimeError):
@@ -44,10 +45,12 @@ class Opts(C.Structure):
         ("workspace", C.c_void_p),
         ("workspace_bytes", C.c_size_t),
         ("mu", C.c_double),
+        ("ao_d0", C.c_double),
+        ("teno_ct", C.c_double),
     ]
 
 
-_OPT_CONSTS = ("C", "eps", "C0", "c1_tau", "c2_tau", "adm_delta", "mu")
+_OPT_CONSTS = ("C", "eps", "C0", "c1_tau", "c2_tau", "adm_delta", "mu", "ao_d0", "teno_ct")
 
 
 def _set_consts(o: Opts, consts: dict) -> None:
@@ -299,9 +302,10 @@ def gks_batch_destroy(b):
 class Batch:
     """Handle wrapper of the batched 2D mode."""
 
-    def __init__(self, nx, ny, hs, gamma=1.4, bc=BC_TRANSMISSIVE, precision=1, stream=None, **consts):
+    def __init__(self, nx, ny, hs, gamma=1.4, bc=BC_TRANSMISSIVE, precision=1, limiter=0, stream=None, **consts):
         o = default_opts()
         o.precision = precision
+        o.limiter = limiter
         _set_consts(o, consts)
         sp = _stream_ptr(stream)
         o.stream = sp.value if sp is not None else None

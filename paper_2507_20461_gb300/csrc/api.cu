@@ -187,6 +187,8 @@ void gks_default_opts(gks_opts_t *o)
     o->c1_tau = 0.05;
     o->c2_tau = 1.0;
     o->adm_delta = 0.3;
+    o->ao_d0 = 0.85;
+    o->teno_ct = 1e-6;
 }
 
 size_t gks_workspace_bytes(const gks_grid_t *grid, int precision)
@@ -233,7 +235,9 @@ int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const
     gks_default_opts(&o);
     if (opts) o = *opts;
     if (o.precision != 0 && o.precision != 1) return fail(nullptr, GKS_ERR_ARG, "precision must be 0 or 1");
-    if (o.limiter != 0 && o.limiter != 1) return fail(nullptr, GKS_ERR_ARG, "limiter must be 0 or 1");
+    if (o.limiter < 0 || o.limiter > 3) return fail(nullptr, GKS_ERR_ARG, "limiter must be 0..3");
+    if (o.limiter >= 2 && (!(o.ao_d0 > 0.0) || !(o.ao_d0 < 1.0) || !(o.teno_ct > 0.0) || !(o.teno_ct < 1.0)))
+        return fail(nullptr, GKS_ERR_ARG, "ao_d0 and teno_ct must lie in (0, 1)");
     if (!(o.C > 0.0) || !(o.eps > 0.0) || !(o.C0 > 0.0) || !(o.c1_tau >= 0.0) || !(o.c2_tau >= 0.0) ||
         !(o.adm_delta >= 0.0) || !(o.adm_delta < 1.0))
         return fail(nullptr, GKS_ERR_ARG, "invalid scheme constants");
@@ -332,6 +336,8 @@ int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const
     P.eps = o.eps;
     P.C0 = o.C0;
     P.adm = o.adm_delta;
+    P.d0 = o.ao_d0;
+    P.ct = o.teno_ct;
     P.fp.gamma = gamma;
     P.fp.c1 = o.c1_tau;
     P.fp.c2 = o.c2_tau;

@@ -94,6 +94,8 @@ void make_kp(gks::KP &P, int nx, int ny, double h, double gamma, int bc, const g
     P.eps = o.eps;
     P.C0 = o.C0;
     P.adm = o.adm_delta;
+    P.d0 = o.ao_d0;
+    P.ct = o.teno_ct;
     P.fp.gamma = gamma;
     P.fp.c1 = o.c1_tau;
     P.fp.c2 = o.c2_tau;
@@ -257,6 +259,9 @@ int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs,
     gks_default_opts(&o);
     if (opts) o = *opts;
     if (o.precision != 0 && o.precision != 1) return bfail(nullptr, GKS_ERR_ARG, "precision must be 0 or 1");
+    if (o.limiter < 0 || o.limiter > 3) return bfail(nullptr, GKS_ERR_ARG, "limiter must be 0..3");
+    if (o.limiter >= 2 && (!(o.ao_d0 > 0.0) || !(o.ao_d0 < 1.0) || !(o.teno_ct > 0.0) || !(o.teno_ct < 1.0)))
+        return bfail(nullptr, GKS_ERR_ARG, "ao_d0 and teno_ct must lie in (0, 1)");
     if (o.workspace) return bfail(nullptr, GKS_ERR_UNSUPPORTED, "batched mode allocates its own workspace");
     if (o.mu != 0.0) return bfail(nullptr, GKS_ERR_UNSUPPORTED, "batched mode solves the Euler equations only (mu = 0)");
     for (int g = 0; g < nbatch; ++g)

@@ -63,7 +63,7 @@ struct KP {
     int n[3];
     int bcs[3][2]; /* per axis, low / high side: 0 periodic (both sides),
                       1 transmissive, 2 reflective (slip), 3 no-slip wall */
-    int limiter; /* 0 GENO, 1 linear */
+    int limiter; /* 0 GENO, 1 linear, 2 WENO-Z, 3 TENO */
     long ncell;
     long nface[3];
     long foff[3];
@@ -72,9 +72,10 @@ struct KP {
     long next;
     double h, ih, gamma;
     double C, itanhC, eps, C0, adm;
+    double d0, ct; /* WENO-Z / TENO: linear weight of the high-order candidate, TENO cut-off */
     FluxParams fp;
     /* FP32 copies for the mixed-precision kernels (fill with finalize_kp) */
-    float fh, fih, fgm1, fC, fitanhC, feps, fC0, fadm;
+    float fh, fih, fgm1, fC, fitanhC, feps, fC0, fadm, fd0, fct;
     /* index decompositions (fill with finalize_kp; every index space of a
      * launch is below 2^32): cells per axis, extended box, per face
      * direction its two leading extents and its face count */
@@ -98,6 +99,8 @@ inline void finalize_kp(KP &P)
     P.fitanhC = (float)P.itanhC;
     P.feps = (float)P.eps;
     P.fC0 = (float)P.C0;
+    P.fd0 = (float)P.d0;
+    P.fct = (float)P.ct;
     for (int a = 0; a < 3; ++a) P.dn[a] = make_fdiv((unsigned)P.n[a]);
     P.dext[0] = make_fdiv((unsigned)P.ext[0]);
     P.dext[1] = make_fdiv((unsigned)P.ext[1]);
@@ -234,6 +237,48 @@ __device__ __forceinline__ R chi_of(const KP &P, R ISt, R ISH, R ISL, int r)
     return RT<R>::tanh_(pick<R>(P.C, P.fC) * alpha) * pick<R>(P.itanhC, P.fitanhC);
 }
 
+/* WENO-Z (limiter 2, Eq. wgt-WENO-Z) or TENO (limiter 3, Eq. wgt-TENO-1 with
+ * the exponent 7 and Eq. wgt-TENO-2) weights over K + 1 candidates: 0 is
+ * the high-order polynomial (indicator IS^H), 1..K the sub-stencil
+ * polynomials; linear weights d, tau_Z = IS^tau.  TENO's (1/(IS + eps))^7 is
+ * taken relative to the smallest indicator, (IS_min + eps) / (IS_k + eps) to
+ * the 7th, which leaves the normalised gamma_k unchanged and keeps FP32 from
+ * overflowing. */
+template <typename R, int K>
+__device__ __forceinline__ void ao_weights(const KP &P, const R *d, const R *IS, R tau, R *w)
+{
+    const R eps = pick<R>(P.eps, P.feps);
+    R s = R(0);
+    if (P.limiter == 2) {
+#pragma unroll
+        for (int k = 0; k <= K; ++k) {
+            w[k] = d[k] * (R(1) + tau / (IS[k] + eps));
+            s += w[k];
+        }
+    } else {
+        R m = IS[0];
+#pragma unroll
+        for (int k = 1; k <= K; ++k) m = fmin(m, IS[k]);
+        R g[K + 1], gs = R(0);
+#pragma unroll
+        for (int k = 0; k <= K; ++k) {
+            const R r = (m + eps) / (IS[k] + eps);
+            const R r2 = r * r;
+            g[k] = r2 * r2 * r2 * r;
+            gs += g[k];
+        }
+        const R cut = pick<R>(P.ct, P.fct) * gs;
+#pragma unroll
+        for (int k = 0; k <= K; ++k) {
+            w[k] = (g[k] <= cut) ? R(0) : d[k];
+            s += w[k];
+        }
+    }
+    const R is = R(1) / s;
+#pragma unroll
+    for (int k = 0; k <= K; ++k) w[k] *= is;
+}
+
 template <typename R, int M>
 __device__ __forceinline__ bool admissible(const R *w, const R *wc, R gm1, R delta)
 {
@@ -266,6 +311,27 @@ __device__ __forceinline__ void geno1d_blend(const KP &P, const R (*a)[2], const
     const R ISH = fmax(IS[0], fmax(IS[1], IS[2]));
     const R ISL = fmin(IS[0], fmin(IS[1], IS[2]));
     const R ISt = RT<R>::abs_(R(0.5) * (IS[1] + IS[2]) - IS[0]);
+    if (P.limiter >= 2) {
+        /* WENO-Z / TENO in the adaptive-order combination:
+         * (w0/d0) q^H + sum_k (w_k - (w0/d0) d_k) p_k, the sub-stencils sharing
+         * 1 - d0 in GENO's low-order proportions (1, C0, 1) */
+        const R d0 = pick<R>(P.d0, P.fd0), C0 = pick<R>(P.C0, P.fC0);
+        const R dl = (R(1) - d0) / (C0 + R(2));
+        const R d[4] = {d0, dl, dl * C0, dl};
+        const R I4[4] = {ISH, IS[0], IS[1], IS[2]};
+        R w[4];
+        ao_weights<R, 3>(P, d, I4, ISt, w);
+        const R chi = w[0] / d0;
+        val = chi * qv;
+        der = chi * qd;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const R ck = w[k + 1] - chi * d[k + 1];
+            val += ck * pv[k];
+            der += ck * pd[k];
+        }
+        return;
+    }
     const R chi = P.limiter ? R(1) : chi_of<R>(P, ISt, ISH, ISL, 2);
     const R eps = pick<R>(P.eps, P.feps);
     const R w0 = R(1) / ((IS[0] + eps) * (IS[0] + eps));
@@ -479,10 +545,11 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R
         }
         R c[NC];
         Cubic<R, M>::fit(d, c);
-        R chi = R(1), gb[M];
+        /* blended cubic: chi c, plus lin on the linear monomials */
+        R chi = R(1), lin[M];
 #pragma unroll
-        for (int a = 0; a < M; ++a) gb[a] = R(0);
-        if (!P.limiter) {
+        for (int a = 0; a < M; ++a) lin[a] = R(0);
+        if (P.limiter != 1) {
             R ISH, ISt;
             Cubic<R, M>::ind(c, ISH, ISt);
             /* linear sub-polynomials on {cell, neighbour q}: g_e = (s dW + D_e)/2, g_t = D_t */
@@ -500,35 +567,57 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R
                 }
                 IS[q] = sum;
             }
-            R smin = IS[0], smax = IS[0], ssum = R(0);
+            if (P.limiter == 0) {
+                R smin = IS[0], smax = IS[0], ssum = R(0);
 #pragma unroll
-            for (int q = 0; q < 2 * M; ++q) {
-                smin = fmin(smin, IS[q]);
-                smax = fmax(smax, IS[q]);
-                ssum += IS[q];
+                for (int q = 0; q < 2 * M; ++q) {
+                    smin = fmin(smin, IS[q]);
+                    smax = fmax(smax, IS[q]);
+                    ssum += IS[q];
+                }
+                const R ISL = (ssum - smin - smax) * R(1.0 / (2 * M - 2));
+                chi = chi_of<R>(P, ISt, ISH, ISL, 3);
+                const R eps = pick<R>(P.eps, P.feps);
+                R ws = R(0);
+#pragma unroll
+                for (int q = 0; q < 2 * M; ++q) {
+                    const R wq = R(1) / ((IS[q] + eps) * (IS[q] + eps));
+                    ws += wq;
+#pragma unroll
+                    for (int a = 0; a < M; ++a) lin[a] += wq * g[q][a];
+                }
+                const R iws = R(1) / ws;
+#pragma unroll
+                for (int a = 0; a < M; ++a) lin[a] = (R(1) - chi) * (lin[a] * iws);
+            } else {
+                /* WENO-Z / TENO, adaptive-order combination: (w0/d0) p^3 +
+                 * sum_q (w_q - (w0/d0) d_q) p_q, the 2m linear polynomials
+                 * sharing 1 - d0 equally */
+                const R d0 = pick<R>(P.d0, P.fd0), dq = (R(1) - d0) * R(1.0 / (2 * M));
+                R d[2 * M + 1], I[2 * M + 1], w[2 * M + 1];
+                d[0] = d0;
+                I[0] = ISH;
+#pragma unroll
+                for (int q = 0; q < 2 * M; ++q) {
+                    d[q + 1] = dq;
+                    I[q + 1] = IS[q];
+                }
+                ao_weights<R, 2 * M>(P, d, I, ISt, w);
+                chi = w[0] / d0;
+#pragma unroll
+                for (int q = 0; q < 2 * M; ++q) {
+                    const R cq = w[q + 1] - chi * dq;
+#pragma unroll
+                    for (int a = 0; a < M; ++a) lin[a] += cq * g[q][a];
+                }
             }
-            const R ISL = (ssum - smin - smax) * R(1.0 / (2 * M - 2));
-            chi = chi_of<R>(P, ISt, ISH, ISL, 3);
-            const R eps = pick<R>(P.eps, P.feps);
-            R ws = R(0);
-#pragma unroll
-            for (int q = 0; q < 2 * M; ++q) {
-                const R wq = R(1) / ((IS[q] + eps) * (IS[q] + eps));
-                ws += wq;
-#pragma unroll
-                for (int a = 0; a < M; ++a) gb[a] += wq * g[q][a];
-            }
-            const R iws = R(1) / ws;
-#pragma unroll
-            for (int a = 0; a < M; ++a) gb[a] *= iws;
         }
-        /* blended cubic: chi c, plus (1 - chi) gbar on the linear monomials
-         * (coefficient M-1-a multiplies xi_a) */
+        /* (coefficient M-1-a multiplies xi_a) */
         const long base = (long)v * NC;
 #pragma unroll
         for (int kk = 0; kk < NC; ++kk) {
             R b = chi * c[kk];
-            if (kk < M) b += (R(1) - chi) * gb[M - 1 - kk];
+            if (kk < M) b += lin[M - 1 - kk];
             B[(base + kk) * P.next + t] = b;
         }
     }

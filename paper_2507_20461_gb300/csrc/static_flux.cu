@@ -68,6 +68,9 @@ extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc
     gks_default_opts(&o);
     if (opts) o = *opts;
     if (o.precision != 0 || o.mu != 0.0) return GKS_ERR_UNSUPPORTED;
+    if (o.limiter < 0 || o.limiter > 3) return GKS_ERR_ARG;
+    if (o.limiter >= 2 && (!(o.ao_d0 > 0.0) || !(o.ao_d0 < 1.0) || !(o.teno_ct > 0.0) || !(o.teno_ct < 1.0)))
+        return GKS_ERR_ARG;
 
     unsigned char *base = nullptr;
     int r = scratch_address(&base);
@@ -101,6 +104,8 @@ extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc
     P.eps = o.eps;
     P.C0 = o.C0;
     P.adm = o.adm_delta;
+    P.d0 = o.ao_d0;
+    P.ct = o.teno_ct;
     P.fp.gamma = gamma;
     P.fp.c1 = o.c1_tau;
     P.fp.c2 = o.c2_tau;

@@ -39,6 +39,7 @@ def test_default_opts_are_the_papers_constants():
     assert o.C == gold["C"]["value"]
     assert o.eps == gold["eps"]["value"]
     assert o.C0 == gold["C0"]["value"]
+    assert o.teno_ct == gold["teno_ct"]["value"]
     assert o.precision == 0 and o.limiter == 0
 
 

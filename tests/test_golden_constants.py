@@ -17,6 +17,7 @@ def test_oracle_defaults_are_the_papers(oracle):
     assert cfg.C == GOLD["C"]["value"]
     assert cfg.eps == GOLD["eps"]["value"]
     assert cfg.C0 == GOLD["C0"]["value"]
+    assert cfg.teno_ct == GOLD["teno_ct"]["value"]
 
 
 def test_oracle_uses_r2_in_1d_and_r3_in_multid(oracle):

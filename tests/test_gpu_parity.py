@@ -444,3 +444,54 @@ def test_conservation_periodic(dim, n, precision):
     scale = np.abs(W).sum(axis=ax)
     drift = np.abs(tot - tot0) / scale
     assert drift.max() <= 1e-13, drift
+
+
+@pytest.mark.parametrize("limiter", [2, 3])
+@pytest.mark.parametrize("dim,n", CASES)
+def test_limiter_variants_parity(dim, n, limiter):
+    """WENO-Z (2) and TENO (3) weights: interface states element-wise and one
+    FP64 step against the oracle."""
+    bc = 1
+    W, G, h = _random_smooth(dim, n, 100 + dim, bc)
+    cfg = O.make_cfg(dim, n, h, bc=bc, limiter=limiter)
+    ref = O.reconstruct(cfg, W, G)
+    s = _solver(dim, n, h, bc, limiter=limiter)
+    s.set_state(_dev(W), _dev(G))
+    out = torch.zeros(ref.size, dtype=torch.float64, device=DEV)
+    s.reconstruct(out)
+    got = out.cpu().numpy().reshape(ref.shape)
+    for v in range(dim + 2):
+        scale = np.abs(W[v]).max() + 1e-300
+        np.testing.assert_allclose(got[:, v, 0], ref[:, v, 0], rtol=0, atol=1e-12 * scale)
+        dscale = np.abs(ref[:, v, 1:]).max() + scale / h
+        np.testing.assert_allclose(got[:, v, 1:], ref[:, v, 1:], rtol=0, atol=1e-11 * dscale)
+    dt = 0.4 * h / O.max_wavespeed(cfg, W)
+    Wo, Go = W.copy(), G.copy()
+    assert O.step(cfg, dt, Wo, Go) == 0
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    s.step(dt)
+    s.get_state(Wd, Gd)
+    assert _rel_l1(Wd.cpu().numpy(), Wo).max() <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("limiter", [2, 3])
+def test_limiter_variants_mixed(limiter):
+    """Mixed precision with WENO-Z / TENO weights, 2D quadrants, 10 steps:
+    mean |d rho| against the FP64 oracle within the mixed-precision bar."""
+    n = (40, 36)
+    W, G, h = I.quadrants_2d(36, seed=31, nx=40)
+    cfg = O.make_cfg(2, n, h, bc=1, limiter=limiter)
+    s = _solver(2, n, h, 1, precision=1, limiter=limiter)
+    Wd, Gd = _dev(W), _dev(G)
+    s.set_state(Wd, Gd)
+    Wo, Go = W.copy(), G.copy()
+    for _ in range(10):
+        dt = 0.4 * h / O.max_wavespeed(cfg, Wo)
+        assert O.step(cfg, dt, Wo, Go) == 0
+        s.step(dt)
+    s.get_state(Wd, Gd)
+    d = np.abs(Wd.cpu().numpy()[0] - Wo[0])
+    assert d.mean() <= 1e-5, d.mean()
+    s.close()
