@@ -250,6 +250,26 @@ const char *gks_last_error(gks_handle_t h);
 int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc_t bc, const gks_opts_t *opts, const double *W,
                        const double *G, double dt, double *face_flux, void *stream);
 
+/* How much of the high-order linear reconstruction the nonlinear weights keep,
+ * evaluated by the reconstruction kernels' own device code (Sec. 3.1 path
+ * function, Eq. HLP-weight; Sec. 3.2 ultimate smoothness indicator,
+ * Eq. HLP-sp; Sec. 5.1-5.2 WENO-Z / TENO weights and the linearity parameter
+ * chi = min_k w_k / d_k, Eq. linearity-paprameter).  For each of n sets i:
+ *   IS[i * k .. i * k + k - 1]  the candidates' smoothness indicators
+ *                               (k = 2..8), tau[i] the indicator IS^tau;
+ *   limiter 0 (GENO): chi[i] = tanh(C alpha) / tanh(C) with IS^H = max,
+ *     IS^L = min of the set and exponent r (2 structured, 3 unstructured);
+ *   limiter 2 (WENO-Z, tau_Z = tau[i]) or 3 (TENO, cut-off opts->teno_ct):
+ *     weights over the k candidates with equal linear weights 1/k,
+ *     chi[i] = min_k w_k k;
+ *   limiter 1: chi[i] = 1.
+ * IS, tau and chi are device pointers.  opts (NULL = defaults) supplies C,
+ * eps, teno_ct, and precision (0: FP64 arithmetic, 1: FP32 as in the
+ * mixed-precision kernels).  Runs on `stream` and synchronises it.
+ * GKS_ERR_ARG on bad arguments, GKS_ERR_CUDA on a launch failure. */
+int geno_linearity(const gks_opts_t *opts, int limiter, int r, int k, long n, const double *IS, const double *tau,
+                   double *chi, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Batched mode: many independent 2D grids of uneven sizes              */
 /* ------------------------------------------------------------------ */

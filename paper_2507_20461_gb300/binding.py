@@ -102,6 +102,7 @@ def lib(build: bool = True):
         "gks_batch_destroy": (C.c_int, [vp]),
         "gks_batch_last_error": (C.c_char_p, [vp]),
         "gks_batch_tuning": (C.c_char_p, [vp]),
+        "geno_linearity": (C.c_int, [op, C.c_int, C.c_int, C.c_int, C.c_long, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -170,6 +171,24 @@ def face_count(grid: Grid) -> int:
 
 def workspace_bytes(grid: Grid, precision: int = 0) -> int:
     return int(lib().gks_workspace_bytes(C.byref(grid), precision))
+
+
+def geno_linearity(IS, tau, chi, limiter: int, r: int = 2, precision: int = 0, stream=None, **consts):
+    """chi[i] of the nonlinear weights for the indicator sets IS[i, :] and
+    IS^tau = tau[i] on the device (see include/genogks.h); device float64
+    tensors IS (n x k), tau (n), chi (n)."""
+    o = default_opts()
+    o.precision = precision
+    _set_consts(o, consts)
+    n, k = IS.shape
+    pi, di = _ptr(IS)
+    pt, dt_ = _ptr(tau)
+    pc, dc = _ptr(chi)
+    if not (di and dt_ and dc):
+        raise ValueError("IS, tau and chi must be device tensors")
+    sp = _stream_ptr(stream)
+    r_ = lib().geno_linearity(C.byref(o), int(limiter), int(r), int(k), int(n), pi, pt, pc, sp)
+    _check(None, r_)
 
 
 def geno_gks_create(grid: Grid, gamma: float, order: int, bc, opts: Opts | None = None):
