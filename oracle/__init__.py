@@ -80,6 +80,10 @@ def lib():
         L.or_max_kin_viscosity.argtypes = [cp, dp]
         L.or_max_kin_viscosity.restype = C.c_double
         L.or_slope_solve.argtypes = [C.c_int, C.c_double, dp, dp, dp]
+        L.or_nc_reconstruct.argtypes = [cp, C.c_int, dp, dp]
+        L.or_nc_flux.argtypes = [cp, C.c_int, dp, dp]
+        L.or_nc_step.argtypes = [cp, C.c_int, C.c_double, dp]
+        L.or_nc_point.argtypes = [cp, C.c_int, dp, dp]
         L.or_moment_matrix.argtypes = [C.c_int, C.c_double, dp, dp]
         L.or_mom_half.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int]
         L.or_mom_half.restype = C.c_double
@@ -163,6 +167,41 @@ def cfl_dt(cfg: Cfg, W: np.ndarray, cfl: float) -> float:
         nu = max_kin_viscosity(cfg, W)
         dt = min(dt, cfl * cfg.h * cfg.h / (2.0 * max(cfg.dim - 1, 1) * nu))
     return dt
+
+
+def nc_reconstruct(cfg: Cfg, order: int, W: np.ndarray) -> np.ndarray:
+    """1D non-compact GENO face states [side][v][face] (Sec. 4.1)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    out = np.zeros((2, 3, cfg.n[0] + 1))
+    if lib().or_nc_reconstruct(C.byref(cfg), int(order), _p(W), _p(out)) != OK:
+        raise RuntimeError("nc_reconstruct failed")
+    return out
+
+
+def nc_point(cfg: Cfg, order: int, u6) -> dict:
+    """left value at x_{j+1/2} from averages at offsets -2..3, with its parts"""
+    u6 = np.ascontiguousarray(u6, dtype=np.float64)
+    out = np.zeros(11)
+    if lib().or_nc_point(C.byref(cfg), int(order), _p(u6), _p(out)) != OK:
+        raise RuntimeError("nc_point failed")
+    k = 3 if order == 5 else 4
+    return {"val": out[0], "qH": out[1], "chi": out[2], "p": out[3 : 3 + k].copy(), "IS": out[7 : 7 + k].copy()}
+
+
+def nc_flux(cfg: Cfg, order: int, W: np.ndarray) -> np.ndarray:
+    """HLLC fluxes [v][face] of the non-compact GENO states."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    out = np.zeros((3, cfg.n[0] + 1))
+    r = lib().or_nc_flux(C.byref(cfg), int(order), _p(W), _p(out))
+    if r != OK:
+        raise RuntimeError(f"nc_flux failed ({r})")
+    return out
+
+
+def nc_step(cfg: Cfg, order: int, dt: float, W: np.ndarray) -> int:
+    """One classical RK4 step of the non-compact scheme, in place."""
+    assert W.flags.c_contiguous and W.dtype == np.float64
+    return lib().or_nc_step(C.byref(cfg), int(order), float(dt), _p(W))
 
 
 def geno1d_point(cfg: Cfg, w5, d5, side: int) -> dict:

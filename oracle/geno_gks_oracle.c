@@ -60,6 +60,10 @@
  *       (w0/d0) q^H + sum_k (w_k - (w0/d0) d_k) p_k with d0 = 0.85 and the
  *       sub-stencils sharing 1 - d0 as GENO's low-order weights do;
  *       tau_Z = IS^tau;
+ *   R16 1D non-compact GENO (5th / 6th order, Sec. 4.1): the sub-stencil
+ *       centred on the reconstruction cell carries d = C0; HLLC with the
+ *       Davis wave-speed bounds; classical RK4; the fallback of R9 and the
+ *       wall fluxes of R8 as for the compact scheme;
  *   R9  a reconstructed interface state whose density or pressure is not
  *       above 0.3 times that of its cell average falls back to the cell
  *       average with zero slopes.
@@ -1047,6 +1051,221 @@ static int flux_all(const or_cfg *c, double dt, const double *fs, double *out)
         off += nf;
     }
     return err ? OR_ERR_NONPHYSICAL : OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 1D non-compact GENO with the HLLC flux and classical RK4 (Sec. 4.1,   */
+/* Sec. 2; reading R16).                                                 */
+/* ------------------------------------------------------------------ */
+/* Left value at the face x_{j+1/2} of cell j from the averages u[i] at
+ * offsets i - 2 (i = 0..5).  order 5: p^4 on {-2..2}, quadratics on
+ * {-2,-1,0}, {-1,0,1}, {0,1,2}; order 6: p^5 on {-2..3}, quadratics on
+ * {-2,-1,0}, {-1,0,1}, cubics on {-1..2}, {0..3}.  IS_k: sum over the
+ * derivative orders 1..deg of int (d^l p_k)^2 on cell j (cell units);
+ * IS^H = max IS_k (Eq. IS-highorder-2), IS^L = min IS_k
+ * (Eq. HLP-IS-loworder-2), IS^tau = |(IS_1 + IS_3)/2 - IS_2|
+ * (Eq. 6th-noncompact-path), r = 2; the sub-stencil centred on cell j,
+ * {-1,0,1}, carries d = C0. */
+static int nc_left_ex(const or_cfg *cfg, int order, const long double *u, long double *val, double *info);
+
+static int nc_left(const or_cfg *cfg, int order, const long double *u, long double *val)
+{
+    return nc_left_ex(cfg, order, u, val, NULL);
+}
+
+/* info (optional): qH, chi, p_k[4], IS_k[4] */
+static int nc_left_ex(const or_cfg *cfg, int order, const long double *u, long double *val, double *info)
+{
+    static const int off5[3][4] = {{-2, -1, 0}, {-1, 0, 1}, {0, 1, 2}};
+    static const int off6[4][4] = {{-2, -1, 0}, {-1, 0, 1}, {-1, 0, 1, 2}, {0, 1, 2, 3}};
+    static const int deg5[3] = {2, 2, 2}, deg6[4] = {2, 2, 3, 3};
+    int nbig = (order == 5) ? 5 : 6, ksub = (order == 5) ? 3 : 4;
+    monset sH, sk[4];
+    monset_build(&sH, 1, nbig - 1);
+    cond c[6];
+    for (int i = 0; i < nbig; ++i) c[i] = (cond){{i - 2, 0, 0}, -1, u[i]};
+    long double aH[8];
+    if (fit_square(&sH, nbig, c, aH)) return -1;
+    long double x[3] = {0.5L, 0, 0};
+    long double qH = poly_eval(&sH, aH, x, -1);
+    long double pk[4], IS[4];
+    for (int k = 0; k < ksub; ++k) {
+        int deg = (order == 5) ? deg5[k] : deg6[k];
+        const int *off = (order == 5) ? off5[k] : off6[k];
+        monset_build(&sk[k], 1, deg);
+        cond ck[4];
+        for (int i = 0; i <= deg; ++i) ck[i] = (cond){{off[i], 0, 0}, -1, u[off[i] + 2]};
+        long double a[8];
+        if (fit_square(&sk[k], deg + 1, ck, a)) return -1;
+        pk[k] = poly_eval(&sk[k], a, x, -1);
+        IS[k] = smooth_ind(&sk[k], a, 1, deg);
+    }
+    long double ISH = IS[0], ISL = IS[0];
+    for (int k = 1; k < ksub; ++k) { if (IS[k] > ISH) ISH = IS[k]; if (IS[k] < ISL) ISL = IS[k]; }
+    long double ISt = fabsl((IS[0] + IS[2]) / 2.0L - IS[1]);
+    long double eps = cfg->eps;
+    long double chi = (cfg->limiter == 1) ? 1.0L : geno_chi(ISt, ISH, ISL, 2, eps, cfg->C);
+    long double ws = 0.0L, qL = 0.0L, wt[4];
+    for (int k = 0; k < ksub; ++k) {
+        long double d = (k == 1) ? cfg->C0 : 1.0L;
+        wt[k] = d / ((IS[k] + eps) * (IS[k] + eps)); /* Eq. HLP-q-loworder */
+        ws += wt[k];
+    }
+    for (int k = 0; k < ksub; ++k) qL += wt[k] / ws * pk[k];
+    *val = chi * qH + (1.0L - chi) * qL; /* Eq. 6th-noncompact-HLP */
+    if (info) {
+        info[0] = (double)qH;
+        info[1] = (double)chi;
+        for (int k = 0; k < 4; ++k) {
+            info[2 + k] = (k < ksub) ? (double)pk[k] : 0.0;
+            info[6 + k] = (k < ksub) ? (double)IS[k] : 0.0;
+        }
+    }
+    return 0;
+}
+
+/* one left value from six averages (offsets -2..3): out = val, qH, chi, p[4], IS[4] */
+int or_nc_point(const or_cfg *c, int order, const double *u6, double *out)
+{
+    if (order != 5 && order != 6) return OR_ERR_ARG;
+    long double u[6], val;
+    for (int i = 0; i < 6; ++i) u[i] = u6[i];
+    if (nc_left_ex(c, order, u, &val, out + 1)) return OR_ERR_ARG;
+    out[0] = (double)val;
+    return OR_OK;
+}
+
+/* Face states of every face f = 0..n (between cells f-1 and f):
+ * st[side][v][f], side 0 left, 1 right; the right state mirrors the stencil
+ * about the face; an inadmissible state falls back to its cell average (R9). */
+static int nc_states(const or_cfg *c, int order, const double *W, double *st)
+{
+    int n = c->n[0], nv = 3;
+    long nf = n + 1;
+    double *Gz = (double *)calloc((size_t)nv * n, sizeof(double));
+    if (!Gz) return OR_ERR_ARG;
+    int err = 0;
+#pragma omp parallel for schedule(static) reduction(| : err)
+    for (long f = 0; f < nf; ++f) {
+        double w6[2][6][3], g[3][5];
+        for (int i = 0; i < 6; ++i) {
+            fetch(c, W, Gz, (int)f - 3 + i, 0, 0, w6[0][i], g); /* cells f-3..f+2, cell f-1 at i = 2 */
+            fetch(c, W, Gz, (int)f + 2 - i, 0, 0, w6[1][i], g); /* mirrored: cell f at i = 2 */
+        }
+        for (int side = 0; side < 2; ++side) {
+            double s3[3];
+            for (int v = 0; v < nv; ++v) {
+                long double u[6], val;
+                for (int i = 0; i < 6; ++i) u[i] = w6[side][i][v];
+                if (nc_left(c, order, u, &val)) { err |= 1; val = 0.0L; }
+                s3[v] = (double)val;
+            }
+            if (!admissible(1, c->gamma, c->adm_delta, s3, w6[side][2]))
+                for (int v = 0; v < nv; ++v) s3[v] = w6[side][2][v];
+            for (int v = 0; v < nv; ++v) st[((long)side * nv + v) * nf + f] = s3[v];
+        }
+    }
+    free(Gz);
+    return err ? OR_ERR_ARG : OR_OK;
+}
+
+/* HLLC flux (Toro) with the Davis wave-speed bounds
+ * SL = min(uL - cL, uR - cR), SR = max(uL + cL, uR + cR) (reading R16) */
+static int hllc(double gamma, const double *L, const double *R, double *F)
+{
+    double rl = L[0], ul = L[1] / rl, pl = (gamma - 1.0) * (L[2] - 0.5 * rl * ul * ul);
+    double rr = R[0], ur = R[1] / rr, pr = (gamma - 1.0) * (R[2] - 0.5 * rr * ur * ur);
+    if (!(rl > 0.0) || !(rr > 0.0) || !(pl > 0.0) || !(pr > 0.0)) return -1;
+    double cl = sqrt(gamma * pl / rl), cr = sqrt(gamma * pr / rr);
+    double SL = fmin(ul - cl, ur - cr), SR = fmax(ul + cl, ur + cr);
+    double Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) / (rl * (SL - ul) - rr * (SR - ur));
+    double FL[3] = {rl * ul, rl * ul * ul + pl, ul * (L[2] + pl)};
+    double FR[3] = {rr * ur, rr * ur * ur + pr, ur * (R[2] + pr)};
+    if (0.0 <= SL) {
+        for (int v = 0; v < 3; ++v) F[v] = FL[v];
+    } else if (0.0 <= Ss) {
+        double k = rl * (SL - ul) / (SL - Ss);
+        double Us[3] = {k, k * Ss, k * (L[2] / rl + (Ss - ul) * (Ss + pl / (rl * (SL - ul))))};
+        for (int v = 0; v < 3; ++v) F[v] = FL[v] + SL * (Us[v] - L[v]);
+    } else if (0.0 <= SR) {
+        double k = rr * (SR - ur) / (SR - Ss);
+        double Us[3] = {k, k * Ss, k * (R[2] / rr + (Ss - ur) * (Ss + pr / (rr * (SR - ur))))};
+        for (int v = 0; v < 3; ++v) F[v] = FR[v] + SR * (Us[v] - R[v]);
+    } else {
+        for (int v = 0; v < 3; ++v) F[v] = FR[v];
+    }
+    return 0;
+}
+
+/* HLLC fluxes F[v][f] of every face; walls carry no mass or energy flux (R8) */
+static int nc_fluxes(const or_cfg *c, int order, const double *W, double *F)
+{
+    int n = c->n[0];
+    long nf = n + 1;
+    double *st = (double *)malloc(sizeof(double) * 2 * 3 * nf);
+    if (!st) return OR_ERR_ARG;
+    int r = nc_states(c, order, W, st);
+    int err = 0;
+    if (!r) {
+        for (long f = 0; f < nf; ++f) {
+            double L[3], R[3], Fv[3];
+            for (int v = 0; v < 3; ++v) { L[v] = st[v * nf + f]; R[v] = st[(3 + v) * nf + f]; }
+            if (hllc(c->gamma, L, R, Fv)) { err = 1; break; }
+            int wall = (f == 0) ? c->bcs[0] : (f == n) ? c->bcs[1] : -1;
+            if (wall >= 2) Fv[0] = Fv[2] = 0.0;
+            for (int v = 0; v < 3; ++v) F[v * nf + f] = Fv[v];
+        }
+    }
+    free(st);
+    return r ? r : (err ? OR_ERR_NONPHYSICAL : OR_OK);
+}
+
+int or_nc_reconstruct(const or_cfg *c, int order, const double *W, double *st)
+{
+    if (check_cfg(c) || c->dim != 1 || (order != 5 && order != 6)) return OR_ERR_ARG;
+    return nc_states(c, order, W, st);
+}
+
+int or_nc_flux(const or_cfg *c, int order, const double *W, double *F)
+{
+    if (check_cfg(c) || c->dim != 1 || (order != 5 && order != 6)) return OR_ERR_ARG;
+    return nc_fluxes(c, order, W, F);
+}
+
+/* classical four-stage fourth-order Runge-Kutta step with
+ * L(U)_j = -(F_{j+1/2} - F_{j-1/2}) / h */
+int or_nc_step(const or_cfg *c, int order, double dt, double *W)
+{
+    if (check_cfg(c) || c->dim != 1 || (order != 5 && order != 6) || !(dt > 0.0)) return OR_ERR_ARG;
+    int n = c->n[0];
+    long nf = n + 1;
+    double *F = (double *)malloc(sizeof(double) * 3 * nf);
+    double *U = (double *)malloc(sizeof(double) * 3 * n);
+    double *K = (double *)malloc(sizeof(double) * 4 * 3 * n);
+    int r = OR_ERR_ARG;
+    if (!F || !U || !K) goto done;
+    static const double a[4] = {0.0, 0.5, 0.5, 1.0}, b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    for (int s = 0; s < 4; ++s) {
+        for (long i = 0; i < 3L * n; ++i) U[i] = W[i] + (s ? a[s] * dt * K[(s - 1) * 3 * n + i] : 0.0);
+        r = nc_fluxes(c, order, U, F);
+        if (r) goto done;
+        for (int v = 0; v < 3; ++v)
+            for (int j = 0; j < n; ++j) K[s * 3 * n + v * n + j] = -(F[v * nf + j + 1] - F[v * nf + j]) / c->h;
+    }
+    for (int v = 0; v < 3; ++v)
+        for (int j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int s = 0; s < 4; ++s) acc += b[s] * K[s * 3 * n + v * n + j];
+            W[v * n + j] += dt * acc;
+        }
+    for (int j = 0; j < n; ++j) {
+        double w[3] = {W[j], W[n + j], W[2 * n + j]};
+        if (!(w[0] > 0.0) || !(pressure(1, c->gamma, w) > 0.0)) { r = OR_ERR_NONPHYSICAL; goto done; }
+    }
+    r = OR_OK;
+done:
+    free(F); free(U); free(K);
+    return r;
 }
 
 /* ------------------------------------------------------------------ */

@@ -1,5 +1,5 @@
-"""Generate ``geno_coeffs.cuh``: the fixed linear maps of the compact GENO
-reconstruction, derived in exact rational arithmetic (sympy) and emitted as
+"""Generate ``geno_coeffs.cuh``: the fixed linear maps of the GENO
+reconstructions (compact and 1D non-compact), derived in exact rational arithmetic (sympy) and emitted as
 straight-line device code.
 
 Run ``python gen_coeffs.py`` after changing the stencils; the output is
@@ -110,6 +110,61 @@ def gen_1d(lines):
     lines.append(f"    der = {ccode(der)};")
     lines.append("}")
     lines.append("")
+
+
+# ------------------------------------------------- 1D non-compact (Sec. 4.1)
+def _avg_poly(offsets, deg):
+    """polynomial of degree deg (cell units, cell j = [-1/2, 1/2]) with the
+    given cell averages u_o, o in offsets (deg + 1 of them)"""
+    cs = sp.symbols(f"b0:{deg + 1}")
+    p = sum(c * x**k for k, c in enumerate(cs))
+    us = [sp.Symbol(f"u{o + 2}") for o in offsets]
+    sol = sp.solve([sp.Eq(cell_avg(p, (o,), 1), u) for o, u in zip(offsets, us)], cs, dict=True)[0]
+    return sp.expand(p.subs(sol))
+
+
+def _js_indicator(P, deg):
+    """sum_(l=1..deg) int_cell (d^l P / dxi^l)^2 (Jiang-Shu, cell units)"""
+    r = sp.Integer(0)
+    for l in range(1, deg + 1):
+        r += sp.integrate(sp.expand(sp.diff(P, x, l) ** 2), (x, -half, half))
+    return sp.expand(r)
+
+
+def gen_noncompact(lines):
+    """Left interface value at x_{j+1/2} of the non-compact GENO schemes:
+    order 5: high-order p^4 on {j-2..j+2}, quadratics on {j-2,j-1,j},
+    {j-1,j,j+1}, {j,j+1,j+2} (the 5th-order WENO stencils);
+    order 6: p^5 on {j-2..j+3}, quadratics on {j-2,j-1,j}, {j-1,j,j+1},
+    cubics on {j-1..j+2}, {j..j+3}.  Inputs u[i] = average at offset i - 2
+    (minus any constant: every polynomial reproduces constants); the right
+    value is the same map applied to the mirrored stencil."""
+    for order, big, subs in (
+        (5, list(range(-2, 3)), [((-2, -1, 0), 2), ((-1, 0, 1), 2), ((0, 1, 2), 2)]),
+        (6, list(range(-2, 4)), [((-2, -1, 0), 2), ((-1, 0, 1), 2), ((-1, 0, 1, 2), 3), ((0, 1, 2, 3), 3)]),
+    ):
+        PH = _avg_poly(big, len(big) - 1)
+        exprs = [PH.subs(x, half)]
+        names = ["qH"]
+        for k, (offs, deg) in enumerate(subs):
+            Pk = _avg_poly(list(offs), deg)
+            exprs.append(Pk.subs(x, half))
+            names.append(f"p[{k}]")
+        for k, (offs, deg) in enumerate(subs):
+            Pk = _avg_poly(list(offs), deg)
+            exprs.append(_js_indicator(Pk, deg))
+            names.append(f"IS[{k}]")
+        usyms = {sp.Symbol(f"u{i}"): sp.Symbol(f"u[{i}]") for i in range(len(big) + 1)}
+        lines.append(f"/* {order}th-order non-compact GENO (Sec. 4.1): left value at x_(j+1/2) of the")
+        lines.append(f" * high-order polynomial (qH) and of the {len(subs)} sub-stencil polynomials (p), and")
+        lines.append(" * the sub-stencils' Jiang-Shu indicators sum_l int (d^l p)^2 (IS), from the")
+        lines.append(" * averages u[i] at offsets i - 2 (cell units). */")
+        lines.append("template <typename R>")
+        lines.append(f"__host__ __device__ __forceinline__ void nc{order}_left(const R *__restrict__ u, R &qH, R *__restrict__ p, R *__restrict__ IS)")
+        lines.append("{")
+        emit_assignments(lines, [sp.expand(e).xreplace(usyms) for e in exprs], names)
+        lines.append("}")
+        lines.append("")
 
 
 # --------------------------------------------------------------- multi-D
@@ -237,6 +292,7 @@ def main():
         "",
     ]
     gen_1d(lines)
+    gen_noncompact(lines)
     info = {}
     for m in (2, 3):
         info[m] = gen_md(lines, m)
