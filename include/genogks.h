@@ -131,8 +131,14 @@ long gks_face_count(const gks_grid_t *grid);
 /* Create a solver for the Euler equations (opts->mu = 0) or the Navier-Stokes
  * equations (opts->mu > 0) with ratio of specific heats gamma (> 1) on `grid`
  * with boundary condition `bc` on every side.
- * order: 8 in 1D (Sec. 4.2), 4 in 2D/3D (Sec. 4.3); anything else gives
- * GKS_ERR_UNSUPPORTED.  opts may be NULL (defaults).  If opts->workspace is
+ * order: 8 in 1D (Sec. 4.2, the compact GKS), 4 in 2D/3D (Sec. 4.3); in 1D
+ * also 5 or 6: the non-compact GENO finite-volume schemes (Sec. 4.1) with
+ * the HLLC flux and classical four-stage RK4 (FP64, inviscid, limiter 0 or 1;
+ * otherwise GKS_ERR_UNSUPPORTED).  They use the cell averages only: G is
+ * ignored on input and returned unchanged; geno_reconstruct writes zero
+ * derivatives, gks_flux the HLLC flux in the F slot and zeros in the dF/dt
+ * and W(dt/2) slots, and gks_step takes one RK4 step.  Any other order
+ * gives GKS_ERR_UNSUPPORTED.  opts may be NULL (defaults).  If opts->workspace is
  * given it must hold gks_workspace_bytes bytes (else GKS_ERR_OOM) and the
  * library allocates no state memory of its own.  The state starts at zero;
  * set it with gks_set_state.  *out receives the handle. */

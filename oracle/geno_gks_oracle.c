@@ -61,7 +61,10 @@
  *       sub-stencils sharing 1 - d0 as GENO's low-order weights do;
  *       tau_Z = IS^tau;
  *   R16 1D non-compact GENO (5th / 6th order, Sec. 4.1): the sub-stencil
- *       centred on the reconstruction cell carries d = C0; HLLC with the
+ *       centred on the reconstruction cell carries d = C0; IS^tau takes the
+ *       outer-left, outer-right and centred sub-stencils (6th order: S_1,
+ *       S_4, S_2; the printed S_1..S_3 never see the stencil's last cell and
+ *       leave chi = 1 across a jump there); HLLC with the
  *       Davis wave-speed bounds; classical RK4; the fallback of R9 and the
  *       wall fluxes of R8 as for the compact scheme;
  *   R9  a reconstructed interface state whose density or pressure is not
@@ -1063,8 +1066,8 @@ static int flux_all(const or_cfg *c, double dt, const double *fs, double *out)
  * {-2,-1,0}, {-1,0,1}, cubics on {-1..2}, {0..3}.  IS_k: sum over the
  * derivative orders 1..deg of int (d^l p_k)^2 on cell j (cell units);
  * IS^H = max IS_k (Eq. IS-highorder-2), IS^L = min IS_k
- * (Eq. HLP-IS-loworder-2), IS^tau = |(IS_1 + IS_3)/2 - IS_2|
- * (Eq. 6th-noncompact-path), r = 2; the sub-stencil centred on cell j,
+ * (Eq. HLP-IS-loworder-2), IS^tau = |(IS_first + IS_last)/2 - IS_2|
+ * (Eq. 6th-noncompact-path, R16), r = 2; the sub-stencil centred on cell j,
  * {-1,0,1}, carries d = C0. */
 static int nc_left_ex(const or_cfg *cfg, int order, const long double *u, long double *val, double *info);
 
@@ -1102,7 +1105,11 @@ static int nc_left_ex(const or_cfg *cfg, int order, const long double *u, long d
     }
     long double ISH = IS[0], ISL = IS[0];
     for (int k = 1; k < ksub; ++k) { if (IS[k] > ISH) ISH = IS[k]; if (IS[k] < ISL) ISL = IS[k]; }
-    long double ISt = fabsl((IS[0] + IS[2]) / 2.0L - IS[1]);
+    /* IS^tau from the outer-left, the outer-right and the centred
+     * sub-stencil: S_1, S_3, S_2 in 5th order (Eq. 6th-noncompact-path);
+     * in 6th order S_1, S_4, S_2, since S_1..S_3 leave the stencil's last
+     * cell unseen (R16) */
+    long double ISt = fabsl((IS[0] + IS[ksub - 1]) / 2.0L - IS[1]);
     long double eps = cfg->eps;
     long double chi = (cfg->limiter == 1) ? 1.0L : geno_chi(ISt, ISH, ISL, 2, eps, cfg->C);
     long double ws = 0.0L, qL = 0.0L, wt[4];

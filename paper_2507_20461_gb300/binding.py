@@ -361,7 +361,8 @@ class Batch:
 class Solver:
     """Handle wrapper: ``Solver(n=(nx, ny), lo, hi, gamma, bc, precision)``."""
 
-    def __init__(self, n, lo=None, hi=None, gamma=1.4, bc=BC_PERIODIC, precision=0, limiter=0, stream=None, **consts):
+    def __init__(self, n, lo=None, hi=None, gamma=1.4, bc=BC_PERIODIC, precision=0, limiter=0, stream=None, order=None,
+                 **consts):
         self.grid = make_grid(n, lo, hi)
         self.dim = len(n)
         self.nv = self.dim + 2
@@ -373,7 +374,10 @@ class Solver:
         sp = _stream_ptr(stream)
         o.stream = sp.value if sp is not None else None
         self.opts = o
-        self.h = geno_gks_create(self.grid, gamma, 8 if self.dim == 1 else 4, bc, o)
+        if order is None:
+            order = 8 if self.dim == 1 else 4
+        self.order = order
+        self.h = geno_gks_create(self.grid, gamma, order, bc, o)
 
     @property
     def shape(self):

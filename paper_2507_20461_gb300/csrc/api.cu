@@ -164,6 +164,10 @@ int two_stages(gks_ctx *c)
 {
     cudaError_t e;
     if (c->shadows) c->g_stale = 1;
+    if (c->dim == 1 && c->order != 8) {
+        if ((e = gks::nc_launch_step(c)) != cudaSuccess) return cuda_fail(c, e, "RK4 step");
+        return GKS_OK;
+    }
     if ((e = run_flux(c, 0, true)) != cudaSuccess) return cuda_fail(c, e, "stage 1 flux");
     if ((e = run_update(c, 1)) != cudaSuccess) return cuda_fail(c, e, "stage 1 update");
     if ((e = run_flux(c, 1, true)) != cudaSuccess) return cuda_fail(c, e, "stage 2 flux");
@@ -229,8 +233,10 @@ int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const
             return fail(nullptr, GKS_ERR_ARG, "axis %d: periodic on one side only", a);
     }
     const int want = (grid->dim == 1) ? 8 : 4;
-    if (order != want)
-        return fail(nullptr, GKS_ERR_UNSUPPORTED, "order %d is not provided in %dD (use %d)", order, grid->dim, want);
+    const bool noncompact = grid->dim == 1 && (order == 5 || order == 6);
+    if (order != want && !noncompact)
+        return fail(nullptr, GKS_ERR_UNSUPPORTED, "order %d is not provided in %dD (use %d%s)", order, grid->dim, want,
+                    grid->dim == 1 ? ", or 5 / 6 for the non-compact schemes" : "");
     gks_opts_t o;
     gks_default_opts(&o);
     if (opts) o = *opts;
@@ -242,6 +248,8 @@ int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const
         !(o.adm_delta >= 0.0) || !(o.adm_delta < 1.0))
         return fail(nullptr, GKS_ERR_ARG, "invalid scheme constants");
     if (!(o.mu >= 0.0) || !std::isfinite(o.mu)) return fail(nullptr, GKS_ERR_ARG, "viscosity mu must be finite and >= 0");
+    if (noncompact && (o.precision != 0 || o.mu != 0.0 || o.limiter > 1))
+        return fail(nullptr, GKS_ERR_UNSUPPORTED, "the non-compact schemes run in FP64, inviscid, with limiter 0 or 1");
 
     gks_ctx *c = new (std::nothrow) gks_ctx;
     if (!c) return fail(nullptr, GKS_ERR_OOM, "host allocation");

@@ -94,6 +94,10 @@ template <int M> cudaError_t launch_flux(gks_ctx *c, int input, bool sums);
 template <int M> cudaError_t launch_update(gks_ctx *c, int stage);
 template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl);
 template <int M> cudaError_t launch_shadow(gks_ctx *c);
+/* 1D non-compact schemes (order 5 or 6): face states / HLLC fluxes of the
+ * stage input (input 0: W, 1: Ws), and one classical RK4 step */
+cudaError_t nc_launch_faces(gks_ctx *c, int input, double *fs_dev, bool flux);
+cudaError_t nc_launch_step(gks_ctx *c);
 
 inline int ngauss(int m) { return m == 1 ? 1 : (m == 2 ? 2 : 4); }
 inline int ncubic(int m) { return m == 2 ? GENO_NC2 : (m == 3 ? GENO_NC3 : 0); }

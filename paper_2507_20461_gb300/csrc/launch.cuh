@@ -27,6 +27,7 @@ static cudaError_t flux_impl(gks_ctx *c, int input, double *fs_dev, bool flux, b
     const double *W = input ? c->Ws : c->W;
     const double *G = input ? c->Gs : c->G;
     if constexpr (M == 1) {
+        if (c->order != 8) return nc_launch_faces(c, input, fs_dev, flux);
         const unsigned nb = blocks_for(P.n[0] + 1);
         ProfScope ps(c, GKS_KC_FACE);
         if (flux && P.fp.mu > 0.0) face1d_kernel<R, true, true><<<nb, kBlock, 0, c->stream>>>(P, W, G, c->dt, nullptr, ff, c->status);

@@ -179,3 +179,26 @@ def test_compact_beats_noncompact_on_coarse_meshes(oracle):
         cfg6 = oracle.make_cfg(1, (6,), h6, bc=0)
         W6 = _run(oracle, order, W6, cfg6, 2.0, 0.4)
         assert e_compact < np.abs(W6[0] - I.sine_exact_rho(1, 6, 2.0)).mean()
+
+
+@pytest.mark.parametrize("order", [5, 6])
+def test_blast_wave(oracle, order):
+    """Woodward-Colella blast wave (Sec. 6.6) with reflecting walls, N = 400,
+    CFL 0.4, to t = 0.038: both schemes stay admissible (the 6th-order one
+    only with IS^tau over the outer and centred sub-stencils, R16)."""
+    n = 400
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+    W = np.stack([np.ones(n), np.zeros(n), p / (GAMMA - 1)])
+    cfg = oracle.make_cfg(1, (n,), h, bc=2)
+    W = _run(oracle, order, W, cfg, 0.038, 0.4)
+    assert W[0].min() > 0 and abs(W[0].sum() * h - 1.0) < 1e-12
+
+
+def test_sixth_order_sees_a_jump_at_the_stencil_end(oracle):
+    """A jump between offsets 2 and 3 lies only in S_0 and S_4: the path
+    function must still leave the high-order polynomial."""
+    cfg = oracle.make_cfg(1, (8,), 0.1)
+    r = oracle.nc_point(cfg, 6, np.array([0.0, 0.0, 0.0, 0.0, 0.0, 1.0]))
+    assert r["chi"] < 1e-10 and abs(r["val"]) < 1e-10
