@@ -324,6 +324,28 @@ def time_3d(B, torch, steps, dev):
             "workload": "3D 256^3 periodic solenoidal velocity (E(k) ~ k^4 exp(-2(k/4)^2), rms Mach 0.6), mixed precision"}
 
 
+def run_case(n, precision, steps):
+    """A small run of the headline workload for ncu captures: the n^2
+    periodic Fourier-mode + shock state, `steps` CFL steps through the C ABI."""
+    import numpy as np
+    import torch
+
+    from paper_2507_20461_gb300 import binding as B
+    from paper_2507_20461_gb300 import inputs as I
+
+    W, G, h = I.fourier_shocks_2d(n, SEED)
+    s = B.Solver((n, n), bc=B.BC_PERIODIC, precision=precision)
+    Wd = torch.from_numpy(np.ascontiguousarray(W)).cuda()
+    Gd = torch.from_numpy(np.ascontiguousarray(G)).cuda()
+    s.set_state(Wd, Gd)
+    s.step_cfl(CFL, steps)
+    torch.cuda.synchronize()
+    st = s.status()
+    s.close()
+    print(f"case n={n} precision={precision} steps={steps} status={st}")
+    return 0 if st == 0 else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -332,9 +354,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true", help="skip the batched and 3D workloads")
+    ap.add_argument("--case", type=int, default=0, metavar="N",
+                    help="profiling case: N^2 cells of the headline IC, --case-steps CFL steps, then exit (no JSON)")
+    ap.add_argument("--case-precision", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--case-steps", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args.case, args.case_precision, args.case_steps)
 
     import numpy as np
     import torch

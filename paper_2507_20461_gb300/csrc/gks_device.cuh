@@ -170,15 +170,146 @@ __device__ __forceinline__ void psi_mom_s(const Mom<R, M> &T, const R *s, R *out
     out[M + 1] += R(0.5) * e;
 }
 
-/* out[b] = <psi_b u^K T>, T = sum_e s_e u_e (slopes along the face axes) */
-template <typename R, int M, int K>
-__device__ __forceinline__ void psi_mom_T(const Mom<R, M> &T, const R (*s)[M + 2], R *out)
+/* <v^A w^B (S^2)^P> over the transverse variables, S^2 = v^2 + w^2 + xi^2
+ * (w absent for M = 2, v and w for M = 1), P = 0, 1, 2; the factors are
+ * independent Maxwellian moments. */
+template <typename R, int M, int A, int B, int P>
+__device__ __forceinline__ R tv(const Mom<R, M> &T)
 {
+    auto V = [&](int k) -> R {
+        if constexpr (M >= 2) return T.v[k];
+        else return k == 0 ? R(1) : R(0);
+    };
+    auto Wm = [&](int k) -> R {
+        if constexpr (M >= 3) return T.w[k];
+        else return k == 0 ? R(1) : R(0);
+    };
+    const R X1 = T.xi[1], X2 = T.xi[2];
+    if constexpr (P == 0) {
+        return V(A) * Wm(B);
+    } else if constexpr (P == 1) {
+        R r = V(A) * Wm(B) * X1;
+        if constexpr (M >= 2) r += V(A + 2) * Wm(B);
+        if constexpr (M >= 3) r += V(A) * Wm(B + 2);
+        return r;
+    } else {
+        R r = V(A) * Wm(B) * X2;
+        if constexpr (M >= 2) r += V(A + 4) * Wm(B) + R(2) * V(A + 2) * Wm(B) * X1;
+        if constexpr (M >= 3) r += V(A) * Wm(B + 4) + R(2) * V(A) * Wm(B + 2) * X1 + R(2) * V(A + 2) * Wm(B + 2);
+        return r;
+    }
+}
+
+/* Moments of the slope term T = sum_e u_e (s_e . psi) of one Maxwellian:
+ * Wo[b] = <psi_b T> (if Wo) and Fo[b] = <u psi_b T> (if Fo), the u-moments
+ * of T taken from Tm (half or full space).  T is split by powers of u,
+ *   T = T0 + u T1 + u^2 T2 + u^3 T3 (coefficients in the transverse v, w, xi),
+ * the transverse expectations <T_n>, <v_r T_n>, <S^2 T_n> are tabulated once,
+ * and every psi moment is a short dot product with the u-moments:
+ *   <u^K psi_0 T> = sum_n U_(n+K) <T_n>,  <u^K psi_1 T> = sum_n U_(n+1+K) <T_n>,
+ *   <u^K v_r T> = sum_n U_(n+K) <v_r T_n>,
+ *   <u^K psi_E T> = 1/2 sum_n (U_(n+2+K) <T_n> + U_(n+K) <S^2 T_n>). */
+template <typename R, int M>
+__device__ __forceinline__ void slope_moments(const Mom<R, M> &Tm, const R (*s)[M + 2], R *Wo, R *Fo)
+{
+    constexpr int NT = M - 1; /* tangential axes */
+    constexpr int NTa = NT > 0 ? NT : 1;
+    /* transverse tables: E1[t] = <v_t>, E2[t][u] = <v_t v_u>, E3[r][t][u],
+     * E1S[t] = <v_t S^2>, E2S[r][t] = <v_r v_t S^2>, E1S4[t] = <v_t S^4> */
+    R E1[NTa], E2[NTa][NTa], E3[NTa][NTa][NTa], E1S[NTa], E2S[NTa][NTa], E1S4[NTa];
+    const R P2 = tv<R, M, 0, 0, 1>(Tm), P4 = tv<R, M, 0, 0, 2>(Tm);
+    if constexpr (M == 2) {
+        E1[0] = tv<R, M, 1, 0, 0>(Tm);
+        E2[0][0] = tv<R, M, 2, 0, 0>(Tm);
+        E3[0][0][0] = tv<R, M, 3, 0, 0>(Tm);
+        E1S[0] = tv<R, M, 1, 0, 1>(Tm);
+        E2S[0][0] = tv<R, M, 2, 0, 1>(Tm);
+        E1S4[0] = tv<R, M, 1, 0, 2>(Tm);
+    } else if constexpr (M == 3) {
+        E1[0] = tv<R, M, 1, 0, 0>(Tm);
+        E1[1] = tv<R, M, 0, 1, 0>(Tm);
+        E2[0][0] = tv<R, M, 2, 0, 0>(Tm);
+        E2[0][1] = E2[1][0] = tv<R, M, 1, 1, 0>(Tm);
+        E2[1][1] = tv<R, M, 0, 2, 0>(Tm);
+        const R vvv = tv<R, M, 3, 0, 0>(Tm), vvw = tv<R, M, 2, 1, 0>(Tm), vww = tv<R, M, 1, 2, 0>(Tm),
+                www = tv<R, M, 0, 3, 0>(Tm);
+        E3[0][0][0] = vvv;
+        E3[0][0][1] = E3[0][1][0] = E3[1][0][0] = vvw;
+        E3[0][1][1] = E3[1][0][1] = E3[1][1][0] = vww;
+        E3[1][1][1] = www;
+        E1S[0] = tv<R, M, 1, 0, 1>(Tm);
+        E1S[1] = tv<R, M, 0, 1, 1>(Tm);
+        E2S[0][0] = tv<R, M, 2, 0, 1>(Tm);
+        E2S[0][1] = E2S[1][0] = tv<R, M, 1, 1, 1>(Tm);
+        E2S[1][1] = tv<R, M, 0, 2, 1>(Tm);
+        E1S4[0] = tv<R, M, 1, 0, 2>(Tm);
+        E1S4[1] = tv<R, M, 0, 1, 2>(Tm);
+    }
+    /* coefficient polynomials: q_e = s_e,E / 2; a_t = s_0,(1+t) + s_t,1 */
+    const R q0 = R(0.5) * s[0][M + 1];
+    R A[4], Bt[NTa][4], Cn[4];
+    A[3] = q0;
+    Cn[3] = q0 * P2;
+    A[2] = s[0][1];
+    Cn[2] = s[0][1] * P2;
+    A[1] = s[0][0] + q0 * P2;
+    Cn[1] = s[0][0] * P2 + q0 * P4;
+    A[0] = R(0);
+    Cn[0] = R(0);
 #pragma unroll
-    for (int b = 0; b < M + 2; ++b) out[b] = R(0);
-    psi_mom_s<R, M, K + 1, 0, 0>(T, s[0], out);
-    if constexpr (M >= 2) psi_mom_s<R, M, K, 1, 0>(T, s[1], out);
-    if constexpr (M >= 3) psi_mom_s<R, M, K, 0, 1>(T, s[2], out);
+    for (int r = 0; r < NT; ++r) {
+        Bt[r][3] = q0 * E1[r];
+        Bt[r][2] = s[0][1] * E1[r];
+        Bt[r][1] = s[0][0] * E1[r] + q0 * E1S[r];
+        Bt[r][0] = R(0);
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const R qt = R(0.5) * s[1 + t][M + 1];
+        const R at = s[0][2 + t] + s[1 + t][1];
+        A[2] += qt * E1[t];
+        Cn[2] += qt * E1S[t];
+        A[1] += at * E1[t];
+        Cn[1] += at * E1S[t];
+        A[0] += s[1 + t][0] * E1[t] + qt * E1S[t];
+        Cn[0] += s[1 + t][0] * E1S[t] + qt * E1S4[t];
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            A[0] += s[1 + t][2 + u] * E2[t][u];
+            Cn[0] += s[1 + t][2 + u] * E2S[t][u];
+        }
+#pragma unroll
+        for (int r = 0; r < NT; ++r) {
+            Bt[r][2] += qt * E2[r][t];
+            Bt[r][1] += at * E2[r][t];
+            Bt[r][0] += s[1 + t][0] * E2[r][t] + qt * E2S[r][t];
+#pragma unroll
+            for (int u = 0; u < NT; ++u) Bt[r][0] += s[1 + t][2 + u] * E3[r][t][u];
+        }
+    }
+    const R *U = Tm.u;
+#pragma unroll
+    for (int K = 0; K < 2; ++K) {
+        R *o = K ? Fo : Wo;
+        if (!o) continue;
+        R o0 = R(0), o1 = R(0), oE = R(0);
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            o0 += U[n + K] * A[n];
+            o1 += U[n + 1 + K] * A[n];
+            oE += U[n + 2 + K] * A[n] + U[n + K] * Cn[n];
+        }
+        o[0] = o0;
+        o[1] = o1;
+#pragma unroll
+        for (int r = 0; r < NT; ++r) {
+            R b = R(0);
+#pragma unroll
+            for (int n = 0; n < 4; ++n) b += U[n + K] * Bt[r][n];
+            o[2 + r] = b;
+        }
+        o[M + 1] = R(0.5) * oE;
+    }
 }
 
 /* Micro-slope a (coefficients on 1, u, v, w, (|u|^2+xi^2)/2) with <a psi> = r,
@@ -350,11 +481,9 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
     }
     /* moments carrying the spatial slopes */
     R FT0[NV], FTl[NV], FTr[NV], WTl[NV], WTr[NV];
-    psi_mom_T<R, M, 1>(T0, s0, FT0);
-    psi_mom_T<R, M, 1>(Tl, sl, FTl);
-    psi_mom_T<R, M, 1>(Tr, sr, FTr);
-    psi_mom_T<R, M, 0>(Tl, sl, WTl);
-    psi_mom_T<R, M, 0>(Tr, sr, WTr);
+    slope_moments<R, M>(T0, s0, nullptr, FT0);
+    slope_moments<R, M>(Tl, sl, WTl, FTl);
+    slope_moments<R, M>(Tr, sr, WTr, FTr);
 
     /* collision times and time integrals */
     const R pl = Pl.p, pr = Pr.p;
