@@ -35,9 +35,17 @@ WORKLOAD = "2D Euler 2048x2048 periodic, 16 random-phase density modes (k<=8) + 
 # Algorithmic work per unit of the dominant kernel (face_flux_kernel), counted
 # by ncu (2 x FMA + ADD + MUL instructions of the pipe) on a 256^2 case in
 # which every face Gauss point is evaluated exactly once:
-#   mixed path: 2004 FP32 flops per face Gauss point;
-#   FP64 path:  2368 FP64 flops per face Gauss point.
-FLOPS_PER_FACE_GP = {"mixed": 2004.0, "fp64": 2368.0}
+#   mixed path: 1764 FP32 flops per face Gauss point;
+#   FP64 path:  2021 FP64 flops per face Gauss point (mean of the stages).
+# (profiles/face_flux_flops_2d_256.md)
+FLOPS_PER_FACE_GP = {"mixed": 1764.0, "fp64": 2021.0}
+# DRAM bytes (read + write) per launch of the face-flux kernel, from one ncu
+# capture each (profiles/face_flux_mixed_2d_1024_full.md,
+# profiles/face_flux_fp64_2d_256_full.md), scaled to the 2048^2 launch by
+# the Gauss points it processes (the traffic is the coefficient array read
+# about once plus the face sums written, both proportional to the grid).
+TRAFFIC_PER_FLUX_LAUNCH = {"mixed": 201.68e6 * (2049 * 2048) / (1025 * 1024),
+                           "fp64": 21.265e6 * (2049 * 2048) / (257 * 256)}
 # Algorithmic HBM bytes per cell-update of the whole step (FP64 state,
 # stage buffers, accumulator), 2D: 60 doubles.
 BYTES_PER_CELL_UPDATE = 480.0
@@ -474,11 +482,11 @@ def main():
         },
         "fp64": {"value": value64, "ms_per_step": ms_fp64, "steps": steps64,
                  "roofline": {"bound": "alu", "achieved": achieved64, "peak": fp64_peak, "unit": "TFLOP/s",
-                              "frac": achieved64 / fp64_peak, "traffic": None}},
+                              "frac": achieved64 / fp64_peak, "traffic": TRAFFIC_PER_FLUX_LAUNCH["fp64"]}},
         "l1_density_mixed_vs_fp64": l1,
         "hbm_roofline_frac": hbm_frac,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak, "traffic": TRAFFIC_PER_FLUX_LAUNCH["mixed"],
                      "kernel": "face_flux_kernel<float,2,D,true>",
                      "peak_source": "FP32: SMs x 128 lanes x 2 flop x max SM clock"},
         "kernel_ms": {name: prof_mixed[k][1] / max(prof_mixed[k][0], 1) for k, name in
