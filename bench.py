@@ -354,6 +354,38 @@ def run_case(n, precision, steps):
     return 0 if st == 0 else 1
 
 
+def time_tgv(B, torch, steps, dev):
+    """Navier-Stokes: the Taylor-Green vortex (u0 = 1, Ma 0.1, Re = 1600 with
+    L0 = 2 pi, Prandtl 1) on 256^3 periodic cells of [-pi, pi]^3, mixed
+    precision, through gks_step_cfl with the viscous time-step limit.  Its
+    accuracy is checked by tests/test_gpu_ns.py (energy decay at Re 100)."""
+    import math
+
+    from paper_2507_20461_gb300 import inputs as I
+
+    n = 256
+    mu = 2 * math.pi / 1600.0
+    W, G, h = I.taylor_green_3d(n)
+    s = B.Solver((n, n, n), lo=[-math.pi] * 3, hi=[math.pi] * 3, bc=B.BC_PERIODIC, precision=1, mu=mu)
+    Wd = torch.from_numpy(W).to(dev)
+    Gd = torch.from_numpy(G).to(dev)
+    s.set_state(Wd, Gd)
+    s.step_cfl(CFL, 2)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step_cfl(CFL, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = s.status()
+    s.close()
+    return {"value": n**3 / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps, "status": st,
+            "workload": "3D Taylor-Green vortex 256^3, Navier-Stokes (Re 1600, Ma 0.1, Pr 1), mixed precision"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -430,6 +462,7 @@ def main():
     e2e_val, h2d, d2h = time_e2e(B, torch, W, G, 1, max(2, min(args.steps, 5)), 1, dev)
     batch = time_batch(B, torch, max(3, min(args.steps, 20)), dev) if not args.headline_only else None
     three_d = time_3d(B, torch, max(3, min(args.steps, 10)), dev) if not args.headline_only else None
+    tgv = time_tgv(B, torch, max(3, min(args.steps, 10)), dev) if not args.headline_only else None
 
     peaks, peak_src = _peaks()
     sm_clock = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
@@ -496,6 +529,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "batched_256_grids": batch,
         "three_d_256": three_d,
+        "navier_stokes_tgv_256": tgv,
         "clocks": clk,
         "cpu_baseline": cpu,
         "peaks_source": peak_src,
