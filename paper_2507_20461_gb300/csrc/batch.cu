@@ -109,7 +109,9 @@ long items(const gks::KP &P, int k, int dir)
     case gks::BK_SPEED:
     case gks::BK_UPDATE: return P.ncell;
     case gks::BK_POLY: return P.next;
-    default: return P.nface[dir] * 2;
+    /* face Gauss points, rounded up to whole 128-item groups (the FP32 flux
+     * maps each group to one block; items past the last face write nothing) */
+    default: return (P.nface[dir] * 2 + 127) / 128 * 128;
     }
 }
 
@@ -118,6 +120,9 @@ int build_tiles(gks_batch_ctx *b, int k, long tile)
     /* the previous list may still be read by work on the internal stream */
     cudaError_t se = cudaStreamSynchronize(b->stream);
     if (se != cudaSuccess) return bcuda(b, se, "tile list");
+    /* flux tiles start on 128-item groups (one group = one 128-thread block
+     * of the FP32 face mapping, whose face sums synchronise the block) */
+    if (k == gks::BK_FLUX && tile % 128 != 0) return bfail(b, GKS_ERR_ARG, "flux tiles must be whole 128-item groups");
     std::vector<Tile> v;
     for (int g = 0; g < b->nb; ++g) {
         const gks::KP &P = b->hd[g].P;

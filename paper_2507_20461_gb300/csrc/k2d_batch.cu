@@ -79,8 +79,9 @@ __global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? 6 : 1)) bk_
         const GridDesc &g = gd[T.grid];
         const Src<R> src = stage_src_of<R>(g, stage);
         const double dtv = dt[T.grid];
-        /* FP32: per-face Gauss sums, as the single-grid step path (tiles and
-         * blocks hold whole faces: even starts, ends and block sizes) */
+        /* FP32: per-face Gauss sums, as the single-grid step path (tiles are
+         * whole 128-item groups, so every thread runs the same iterations and
+         * t mod 128 is its thread index) */
         constexpr bool fsum = sizeof(R) == sizeof(float);
         if (T.kind == 0) {
             for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x)
@@ -128,6 +129,7 @@ template <typename R> cudaError_t batch_poly(const BatchLaunch &L, const LaunchS
 }
 template <typename R> cudaError_t batch_flux(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st)
 {
+    if (S.block != 128) return cudaErrorInvalidConfiguration; /* the face mapping's group size */
     bk_flux<R><<<S.blocks, S.block, 0, st>>>(L.gd, L.tiles, L.ntiles, stage, L.dt, L.status);
     return cudaGetLastError();
 }

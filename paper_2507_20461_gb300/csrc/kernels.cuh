@@ -649,14 +649,32 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
 {
     constexpr int NV = M + 2, NC = Cubic<R, M>::NC, NG = (M == 2) ? 2 : 4;
     const long nf = P.nface[D];
-    /* FP32: the Gauss points of one face are neighbouring threads (they read
-     * the same two cells' coefficients; measured faster).  FP64: one Gauss
-     * point per warp, so the per-point evaluation does not diverge in this
-     * compute-bound kernel. */
+    /* FP32: each aligned group of 128 items is one block of 4 warps; its NG
+     * consecutive warps take the NG Gauss points of the same 32 faces, so the
+     * Gauss point is warp-uniform (the per-point evaluation does not diverge)
+     * and the two cells' coefficients are shared through L1.  Items past the
+     * last face (the index space is rounded up to whole groups) compute a
+     * valid face and write nothing.  FP64: one Gauss point per half of the
+     * index space. */
     constexpr bool gfast = sizeof(R) == sizeof(float);
     const unsigned tu = (unsigned)t;
-    const int g = gfast ? (int)(tu % NG) : (int)fdiv(P.dnf[D], tu);
-    const long fl = gfast ? (long)(tu / NG) : t - (long)g * nf;
+    int g;
+    long fl;
+    if constexpr (gfast) {
+        g = (int)((tu >> 5) % NG);
+        fl = (long)(tu >> 7) * (128 / NG) + (long)(((tu & 127u) >> 5) / NG) * 32 + (long)(tu & 31u);
+    } else {
+        g = (int)fdiv(P.dnf[D], tu);
+        fl = t - (long)g * nf;
+    }
+    const bool valid = fl < nf && g < NG;
+    /* a masked item evaluates the last face; in FP32 it keeps its warp's
+     * Gauss point (always < NG), which also places it in the face sums'
+     * shared tile below */
+    if (!valid) {
+        fl = nf - 1;
+        if constexpr (!gfast) g = 0;
+    }
     int idx[3];
     unsigned q0, q1;
     idx[0] = (int)fdivmod(P.dface[D][0], (unsigned)fl, q0);
@@ -699,6 +717,7 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
     }
     const long nft = P.nftot, face = P.foff[D] + fl;
     if (!FLUX) {
+        if (!valid) return;
 #pragma unroll
         for (int side = 0; side < 2; ++side)
 #pragma unroll
@@ -742,22 +761,31 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
     if ((idx[D] == 0 && P.bcs[D][0] >= 2) || (idx[D] == P.n[D] && P.bcs[D][1] >= 2))
         F[0] = F[NV - 1] = Ft[0] = Ft[NV - 1] = R(0);
     if constexpr (FSUM) {
-        /* step path in FP32: the face's NG Gauss points sit in neighbouring
-         * lanes; sum them there and store one value per face and quantity,
-         * ff[q][v][face] (q = F, dF/dt, W(dt/2)) */
-        static_assert(gfast, "face sums need the Gauss points in neighbouring lanes");
-        const unsigned lane = threadIdx.x & 31u;
-        const unsigned mask = ((1u << NG) - 1u) << (lane & ~(unsigned)(NG - 1));
+        /* step path in FP32: sum the face's NG Gauss points (the NG warps of
+         * its group, through shared memory; every thread of the block takes
+         * part) in the order (F0 + F1) [+ (F2 + F3)], and store one value per
+         * face and quantity, ff[q][v][face] (q = F, dF/dt, W(dt/2)) */
+        static_assert(gfast, "face sums need the warp-group mapping");
+        __shared__ R xs[3 * NV][128];
+        const int lt = threadIdx.x;
 #pragma unroll
-        for (int o = 1; o < NG; o <<= 1) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                F[v] += __shfl_xor_sync(mask, F[v], o);
-                Ft[v] += __shfl_xor_sync(mask, Ft[v], o);
-                Wh[v] += __shfl_xor_sync(mask, Wh[v], o);
-            }
+        for (int v = 0; v < NV; ++v) {
+            xs[v][lt] = F[v];
+            xs[NV + v][lt] = Ft[v];
+            xs[2 * NV + v][lt] = Wh[v];
         }
-        if (g == 0) {
+        __syncthreads();
+        const int l0 = lt - g * 32; /* this face's Gauss point 0 */
+#pragma unroll
+        for (int q = 0; q < 3 * NV; ++q) {
+            R a = xs[q][l0] + xs[q][l0 + 32];
+            if constexpr (NG == 4) a = a + (xs[q][l0 + 64] + xs[q][l0 + 96]);
+            if (q < NV) F[q] = a;
+            else if (q < 2 * NV) Ft[q - NV] = a;
+            else Wh[q - 2 * NV] = a;
+        }
+        __syncthreads();
+        if (g == 0 && valid) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 int fv = v;
@@ -781,6 +809,7 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
             for (int kk = 0; kk < M; ++kk)
                 if (ax[kk] == v - 1) fv = 1 + kk;
         }
+        if (!valid) continue;
         ff[((long)(0 * NV + v) * NG + g) * nft + face] = F[fv];
         ff[((long)(1 * NV + v) * NG + g) * nft + face] = Ft[fv];
         ff[((long)(2 * NV + v) * NG + g) * nft + face] = Wh[fv];
@@ -800,9 +829,13 @@ __global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? (NS ? 4 : 6
                                                         R *__restrict__ ff, int *__restrict__ status)
 {
     constexpr int NG = (M == 2) ? 2 : 4;
-    /* 128 threads and NG | nface * NG: the NG lanes of a face are all in range or all out */
+    /* 128 threads per block.  FP32: the grid covers whole 128-item groups
+     * (ceil(nface / (128 / NG)) blocks) and every thread runs the item, which
+     * masks the items past the last face (its face sums synchronise the
+     * block).  FP64: one thread per (face, Gauss point). */
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < P.nface[D] * NG) face_flux_item<R, M, D, FLUX, NS, FSUM>(P, src, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
+    if (sizeof(R) == sizeof(float) || t < P.nface[D] * NG)
+        face_flux_item<R, M, D, FLUX, NS, FSUM>(P, src, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
 }
 
 /* ------------------------------------------------------------------ */

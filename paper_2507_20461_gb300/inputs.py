@@ -100,19 +100,19 @@ def quadrants_2d(n: int, seed: int, gamma: float = GAMMA, nx: int | None = None)
     return W, G, h
 
 
-def _fourier_shock_strip(xs, ys, modes, shocks, gamma):
+def _fourier_shock_strip(xs, ys, modes, shocks, gamma, drift=(0.0, 0.0)):
     """Point values on the tensor grid ys x xs (1D arrays): base gas
-    rho = 1 + 0.2/16 sum cos(2 pi k.x + phi), u = 0, p = 1, then each shock in
-    order overwrites its slab with the Rankine-Hugoniot post-shock state of the
-    base gas (moving along the shock normal)."""
+    rho = 1 + 0.2/16 sum cos(2 pi k.x + phi), (u, v) = drift, p = 1, then each
+    shock in order overwrites its slab with the Rankine-Hugoniot post-shock
+    state of the gas at rest (moving along the shock normal)."""
     rho = np.ones((ys.size, xs.size))
     amp = 0.2 / len(modes)
     for (kx, ky, ph) in modes:
         ax = 2 * math.pi * kx * xs + ph
         by = 2 * math.pi * ky * ys
         rho += amp * (np.outer(np.cos(by), np.cos(ax)) - np.outer(np.sin(by), np.sin(ax)))
-    u = np.zeros_like(rho)
-    v = np.zeros_like(rho)
+    u = np.full_like(rho, drift[0])
+    v = np.full_like(rho, drift[1])
     p = np.ones_like(rho)
     base_rho = rho.copy()
     for (nx_, ny_, off, M) in shocks:
@@ -129,7 +129,8 @@ def _fourier_shock_strip(xs, ys, modes, shocks, gamma):
     return rho, u, v, p
 
 
-def fourier_shocks_2d(n: int, seed: int, gamma: float = GAMMA, sub: int | None = None):
+def fourier_shocks_2d(n: int, seed: int, gamma: float = GAMMA, sub: int | None = None,
+                      nshocks: int = 4, drift=(0.0, 0.0)):
     """Periodic [0,1]^2: rho = 1 + 0.2/16 sum_m cos(2 pi k_m.x + phi_m), 1 <= |k_m|_inf <= 8,
     u = 0, p = 1, then four planar shocks (normals from {(1,0),(0,1),(1,1),(1,-1)},
     offset ~ U[0,1), Mach ~ U[1.5, 3]); each shock sets, in a slab of width
@@ -137,6 +138,11 @@ def fourier_shocks_2d(n: int, seed: int, gamma: float = GAMMA, sub: int | None =
     gas (later shocks overwrite earlier ones).  Averages by sub x sub midpoint
     sampling (sub = 8 up to n = 512, else 4), gradients by the Gauss theorem
     with sub samples per face.
+
+    Smooth variant: nshocks < 4 keeps only the first shocks drawn (the draws
+    are unchanged, so the modes are those of the full case) and drift gives
+    the base gas a uniform velocity (the shocks' post-shock states are those
+    of the gas at rest, so drift is meant for nshocks = 0).
     """
     rng = np.random.default_rng(seed)
     modes = []
@@ -149,6 +155,7 @@ def fourier_shocks_2d(n: int, seed: int, gamma: float = GAMMA, sub: int | None =
     for i in range(4):
         nrm = normals[rng.integers(0, 4)]
         shocks.append((nrm[0], nrm[1], rng.uniform(0, 1), rng.uniform(1.5, 3.0)))
+    shocks = shocks[:nshocks]
     if sub is None:
         sub = 8 if n <= 512 else 4
     h = 1.0 / n
@@ -163,16 +170,16 @@ def fourier_shocks_2d(n: int, seed: int, gamma: float = GAMMA, sub: int | None =
     for j0 in range(0, n, rows):
         j1 = min(n, j0 + rows)
         ys_sub = (base[j0:j1, None] + off[None, :] * h).ravel()
-        rho, u, v, p = _fourier_shock_strip(xs_sub, ys_sub, modes, shocks, gamma)
+        rho, u, v, p = _fourier_shock_strip(xs_sub, ys_sub, modes, shocks, gamma, drift)
         cons = _cons(rho, [u, v], p, gamma)  # (nv, (j1-j0)*sub, n*sub)
         W[:, j0:j1] = cons.reshape(nv, j1 - j0, sub, n, sub).mean(axis=(2, 4))
         # x faces: sample x on faces, y on sub-samples
-        rho, u, v, p = _fourier_shock_strip(xs_face, ys_sub, modes, shocks, gamma)
+        rho, u, v, p = _fourier_shock_strip(xs_face, ys_sub, modes, shocks, gamma, drift)
         cf = _cons(rho, [u, v], p, gamma).reshape(nv, j1 - j0, sub, n + 1).mean(axis=2)
         G[0, :, j0:j1] = (cf[:, :, 1:] - cf[:, :, :-1]) / h
         # y faces
         ys_face = np.concatenate([base[j0:j1] - 0.5 * h, [base[j1 - 1] + 0.5 * h]])
-        rho, u, v, p = _fourier_shock_strip(xs_sub, ys_face, modes, shocks, gamma)
+        rho, u, v, p = _fourier_shock_strip(xs_sub, ys_face, modes, shocks, gamma, drift)
         cf = _cons(rho, [u, v], p, gamma).reshape(nv, j1 - j0 + 1, n, sub).mean(axis=3)
         G[1, :, j0:j1] = (cf[:, 1:] - cf[:, :-1]) / h
     return W, G, h
