@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(128) bk_poly(const GridDesc *__restrict__ gd, 
     }
 }
 
-/* same register cap as the single-grid FP32 flux (6 blocks of 128 per SM) */
+/* same register cap as the single-grid 2D FP32 flux (8 blocks of 128 per SM) */
 template <typename R>
-__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? 6 : 1)) bk_flux(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? 8 : 1)) bk_flux(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
                                                int stage, const double *__restrict__ dt, int *__restrict__ status)
 {
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {

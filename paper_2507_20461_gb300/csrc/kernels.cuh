@@ -816,15 +816,13 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
     }
 }
 
-/* 128 threads; the FP32 flux asks for 6 blocks per SM (80 registers, a small
- * spill), measured faster than 127 registers.  (8 blocks, 64 registers, was
- * faster still but moved the FP32 rounding enough to flip a face-state
- * fallback decision against the FP64 oracle on a coarse shock problem.)  The
- * FP64 flux is bound by the FP64 pipe and keeps its registers.  The 3D FP32
- * flux also runs at 6 blocks (measured 8% faster than 4, 3% faster than 8);
- * the Navier-Stokes flux (more live moments) gets 4. */
+/* 128 threads.  Blocks per SM asked of the FP32 flux, measured with the
+ * warp-group mapping: 2D 8 (64 registers; 1.7% faster than 7, 4.5% than 6),
+ * 3D 7 (72 registers; 6.8% faster than 8), Navier-Stokes 5 (more live
+ * moments; 3.4% faster than 4 and 6).  The FP64 flux is bound by the FP64
+ * pipe and keeps its registers. */
 template <typename R, int M, int D, bool FLUX, bool NS = false, bool FSUM = false>
-__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? (NS ? 4 : 6) : 1)) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
+__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? (NS ? 5 : (M == 2 ? 8 : 7)) : 1)) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
                                                         const double *__restrict__ dtp, double *__restrict__ fs,
                                                         R *__restrict__ ff, int *__restrict__ status)
 {
