@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(128) bk_poly(const GridDesc *__restrict__ gd, 
 
 /* same register cap as the single-grid 2D FP32 flux (8 blocks of 128 per SM) */
 template <typename R>
-__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? 8 : 1)) bk_flux(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(128, (flux_blocks_per_sm<R, 2, false>())) bk_flux(const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
                                                int stage, const double *__restrict__ dt, int *__restrict__ status)
 {
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
@@ -171,6 +171,10 @@ int batch_occupancy(int kernel, int precision, int block)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_poly<float> : bk_poly<double>, block, 0);
         break;
     case BK_FLUX:
+        /* its coefficient staging needs a larger shared-memory carveout than
+         * the default to reach the launch bounds' blocks per SM */
+        if (precision) smem_carveout_for(bk_flux<float>, flux_blocks_per_sm<float, 2, false>());
+        else smem_carveout_for(bk_flux<double>, flux_blocks_per_sm<double, 2, false>());
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_flux<float> : bk_flux<double>, block, 0);
         break;
     default:

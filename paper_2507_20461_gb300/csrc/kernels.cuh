@@ -639,6 +639,16 @@ __device__ __forceinline__ long ext_lin(const KP &P, int i, int j, int k)
     return r;
 }
 
+/* The FP32 flux's staging buffer: one per dimension, shared by the
+ * directions (a kernel that runs several directions, such as the batched
+ * flux, holds one buffer, not one per direction). */
+template <int M> __device__ __forceinline__ float *flux_stage()
+{
+    constexpr int NV = M + 2, NG = (M == 2) ? 2 : 4;
+    __shared__ __align__(16) float buf[2 * NV * Cubic<float, M>::NC * (128 / NG)];
+    return buf;
+}
+
 /* one (face, Gauss point) of direction D.  FLUX = false writes the states
  * face_states[side][v][c][g][face] (double, global axes); FLUX = true the
  * fluxes ff[q][v][g][face] (R, global momentum order). */
@@ -681,6 +691,34 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
     idx[1] = (M >= 2) ? (int)fdivmod(P.dface[D][1], q0, q1) : 0;
     idx[2] = (M >= 3) ? (int)q1 : 0;
     const R gm1 = pick<R>(P.fp.gm1, P.fgm1);
+    /* FP32: the blended coefficients of the two cells of the block's faces
+     * are staged in shared memory, stage[side][v * NC + k][face in block].
+     * Each face's NG threads copy a share of its 2 NV NC values with cp.async
+     * (all copies in flight at once, each value read once per face instead
+     * of once per Gauss point, no registers held while they land); the face
+     * sums below reuse the buffer. */
+    constexpr int FB = 128 / NG, NVC = NV * NC;
+    float *stage = nullptr;
+    if constexpr (gfast) stage = flux_stage<M>();
+    const int fb = (int)((((unsigned)threadIdx.x >> 5) / NG) * 32 + (threadIdx.x & 31u));
+    if constexpr (gfast) {
+        constexpr int PARTS = NG / 2, PER = NVC / PARTS;
+        static_assert(NVC % PARTS == 0, "the copies split evenly over a side's threads");
+        const int side = g & 1, part = g >> 1;
+        int ci[3] = {idx[0], idx[1], idx[2]};
+        if (side == 0) ci[D] -= 1;
+        const float *sp = (const float *)B + (long)(part * PER) * P.next + ext_lin<M>(P, ci[0], ci[1], ci[2]);
+        unsigned dp = (unsigned)__cvta_generic_to_shared(stage) + 4u * (unsigned)((side * NVC + part * PER) * FB + fb);
+        __syncthreads(); /* a previous item's readers of the buffer are done */
+#pragma unroll 10
+        for (int k = 0; k < PER; ++k) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dp), "l"(sp) : "memory");
+            sp += P.next;
+            dp += 4u * FB;
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
+    }
     /* interface states, global axes: st[side][v][c], c = 0 value, 1 + e d/dx_e */
     R st[2][NV][M + 1], cw[2][NV];
 #pragma unroll
@@ -689,12 +727,17 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
         if (side == 0) ci[D] -= 1;
         int flip[3];
         const long cl = cell_lin<M>(P, ci[0], ci[1], ci[2], flip);
-        const long ce = ext_lin<M>(P, ci[0], ci[1], ci[2]);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             R c[NC], out[M + 1];
+            if constexpr (gfast) {
 #pragma unroll
-            for (int kk = 0; kk < NC; ++kk) c[kk] = B[((long)v * NC + kk) * P.next + ce];
+                for (int kk = 0; kk < NC; ++kk) c[kk] = stage[(side * NVC + v * NC + kk) * FB + fb];
+            } else {
+                const long ce = ext_lin<M>(P, ci[0], ci[1], ci[2]);
+#pragma unroll
+                for (int kk = 0; kk < NC; ++kk) c[kk] = B[((long)v * NC + kk) * P.next + ce];
+            }
             if (side == 0) CubicEval<R, M, D, 1>::run(g, c, out);
             else CubicEval<R, M, D, 0>::run(g, c, out);
             const R w0 = R(src.w0(v * P.ncell + cl)) * R(ghost_sign<M>(P, flip, v));
@@ -766,8 +809,10 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
          * part) in the order (F0 + F1) [+ (F2 + F3)], and store one value per
          * face and quantity, ff[q][v][face] (q = F, dF/dt, W(dt/2)) */
         static_assert(gfast, "face sums need the warp-group mapping");
-        __shared__ R xs[3 * NV][128];
+        static_assert(3 * NV * 128 <= 2 * NVC * FB, "the face sums fit in the staging buffer");
+        R(*xs)[128] = reinterpret_cast<R(*)[128]>(stage);
         const int lt = threadIdx.x;
+        __syncthreads(); /* every thread has read its coefficients */
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             xs[v][lt] = F[v];
@@ -821,8 +866,13 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
  * 3D 7 (72 registers; 6.8% faster than 8), Navier-Stokes 5 (more live
  * moments; 3.4% faster than 4 and 6).  The FP64 flux is bound by the FP64
  * pipe and keeps its registers. */
+template <typename R, int M, bool NS> constexpr int flux_blocks_per_sm()
+{
+    return sizeof(R) == sizeof(float) ? (NS ? 5 : (M == 2 ? 8 : 7)) : 1;
+}
+
 template <typename R, int M, int D, bool FLUX, bool NS = false, bool FSUM = false>
-__global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? (NS ? 5 : (M == 2 ? 8 : 7)) : 1)) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
+__global__ void __launch_bounds__(128, (flux_blocks_per_sm<R, M, NS>())) face_flux_kernel(KP P, Src<R> src, const R *__restrict__ B,
                                                         const double *__restrict__ dtp, double *__restrict__ fs,
                                                         R *__restrict__ ff, int *__restrict__ status)
 {
@@ -834,6 +884,36 @@ __global__ void __launch_bounds__(128, (sizeof(R) == sizeof(float) ? (NS ? 5 : (
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (sizeof(R) == sizeof(float) || t < P.nface[D] * NG)
         face_flux_item<R, M, D, FLUX, NS, FSUM>(P, src, B, FLUX ? dtp[0] : 0.0, fs, ff, status, t);
+}
+
+/* Shared-memory carveout of a kernel with static shared memory: the smallest
+ * share of the SM's unified L1/shared storage that still holds `blocks`
+ * resident blocks (the driver rounds the preference up to the next supported
+ * capacity; the default can hold fewer blocks than the launch bounds ask
+ * for), so the rest stays L1.  Set once per kernel; a refusal leaves the
+ * default. */
+template <typename K> inline void smem_carveout_for(K kernel, int blocks)
+{
+    cudaFuncAttributes fa;
+    int dev = 0, maxsm = 0, rsv = 0;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess || maxsm <= 0) {
+        (void)cudaGetLastError();
+        return;
+    }
+    const long need = (long)blocks * (long)(fa.sharedSizeBytes + rsv);
+    long pct = (need * 100 + maxsm - 1) / maxsm;
+    if (pct > 100) pct = 100;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)pct) != cudaSuccess)
+        (void)cudaGetLastError();
+}
+
+/* once per instantiation, before its first launch */
+template <typename R, int M, int D, bool FLUX, bool NS = false, bool FSUM = false> inline void face_flux_prepare()
+{
+    static const bool done = (smem_carveout_for(face_flux_kernel<R, M, D, FLUX, NS, FSUM>, flux_blocks_per_sm<R, M, NS>()), true);
+    (void)done;
 }
 
 /* ------------------------------------------------------------------ */

@@ -48,15 +48,15 @@ static cudaError_t flux_impl(gks_ctx *c, int input, double *fs_dev, bool flux, b
     if (d == D) {                                                                                             \
         if constexpr (sizeof(R) == sizeof(float)) {                                                           \
             if (flux && sums && P.fp.mu > 0.0)                                                                \
-                face_flux_kernel<R, M, D, true, true, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+                { face_flux_prepare<R, M, D, true, true, true>(); face_flux_kernel<R, M, D, true, true, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); } \
             else if (flux && sums)                                                                            \
-                face_flux_kernel<R, M, D, true, false, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+                { face_flux_prepare<R, M, D, true, false, true>(); face_flux_kernel<R, M, D, true, false, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); } \
         }                                                                                                     \
         if (flux && !(sizeof(R) == sizeof(float) && sums)) {                                                 \
-            if (P.fp.mu > 0.0) face_flux_kernel<R, M, D, true, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
-            else face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); \
+            if (P.fp.mu > 0.0) { face_flux_prepare<R, M, D, true, true>(); face_flux_kernel<R, M, D, true, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); } \
+            else { face_flux_prepare<R, M, D, true>(); face_flux_kernel<R, M, D, true><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, nullptr, ff, c->status); } \
         }                                                                                                     \
-        if (!flux) face_flux_kernel<R, M, D, false><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, fs_dev, nullptr, c->status); \
+        if (!flux) { face_flux_prepare<R, M, D, false>(); face_flux_kernel<R, M, D, false><<<nb, kBlock, 0, c->stream>>>(P, src, B, c->dt, fs_dev, nullptr, c->status); } \
     }
             GKS_FACE(0)
             GKS_FACE(1)
