@@ -44,8 +44,9 @@ FLOPS_PER_FACE_GP = {"mixed": 1764.0, "fp64": 2021.0}
 # profiles/face_flux_fp64_2d_256_full.md), scaled to the 2048^2 launch by
 # the Gauss points it processes (the traffic is the coefficient array read
 # about once plus the face sums written, both proportional to the grid).
-TRAFFIC_PER_FLUX_LAUNCH = {"mixed": 201.68e6 * (2049 * 2048) / (1025 * 1024),
-                           "fp64": 21.265e6 * (2049 * 2048) / (257 * 256)}
+# None where the kernel has changed since its capture.
+TRAFFIC_PER_FLUX_LAUNCH = {"mixed": 209.06e6 * (2049 * 2048) / (1025 * 1024),
+                           "fp64": None}
 # Algorithmic HBM bytes per cell-update of the whole step (FP64 state,
 # stage buffers, accumulator), 2D: 60 doubles.
 BYTES_PER_CELL_UPDATE = 480.0
