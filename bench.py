@@ -1,7 +1,8 @@
 """Benchmark: cell-updates/s of the compact GKS with GENO reconstruction on the
 2D 2048^2 periodic workload (16 random-phase density modes + 4 planar shocks,
 Mach 1.5-3), mixed precision (FP32 reconstruction/flux, FP64 accumulation)
-against FP64, with the L1 density error of mixed against FP64.
+against FP64, with the density L1 and L-inf errors of mixed against FP64
+after the same 100 CFL steps.
 
 One JSON line on rank 0.  A step is one full two-stage step of every cell
 (gks_step_cfl: device time step, stage 1, stage 2).  `value` is the mixed-
@@ -44,9 +45,8 @@ FLOPS_PER_FACE_GP = {"mixed": 1764.0, "fp64": 2021.0}
 # profiles/face_flux_fp64_2d_256_full.md), scaled to the 2048^2 launch by
 # the Gauss points it processes (the traffic is the coefficient array read
 # about once plus the face sums written, both proportional to the grid).
-# None where the kernel has changed since its capture.
 TRAFFIC_PER_FLUX_LAUNCH = {"mixed": 209.06e6 * (2049 * 2048) / (1025 * 1024),
-                           "fp64": None}
+                           "fp64": 21.266e6 * (2049 * 2048) / (257 * 256)}
 # Algorithmic HBM bytes per cell-update of the whole step (FP64 state,
 # stage buffers, accumulator), 2D: 60 doubles.
 BYTES_PER_CELL_UPDATE = 480.0
@@ -149,6 +149,20 @@ def cpu_baseline(n_sample: int = 256, steps: int = 2):
         "kind": "oracle",
         "sample": f"{n_sample}x{n_sample} periodic grid of the same IC recipe, {steps} FP64 steps (wall {el:.1f} s)",
     }
+
+
+def cpu_single_core(n_sample: int = 64, steps: int = 1):
+    """The same oracle sample on one core: this script re-run with
+    OMP_NUM_THREADS=1 (a fresh process, so the OpenMP runtime starts with one
+    thread)."""
+    import subprocess
+
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", str(n_sample), "--cpu-steps", str(steps)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(f"single-core oracle run failed: {r.stderr[-400:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args):
@@ -399,11 +413,17 @@ def main():
                     help="profiling case: N^2 cells of the headline IC, --case-steps CFL steps, then exit (no JSON)")
     ap.add_argument("--case-precision", type=int, default=1, choices=[0, 1])
     ap.add_argument("--case-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=0, metavar="N",
+                    help="only time the oracle on an N^2 sample of the workload and print its JSON")
+    ap.add_argument("--cpu-steps", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.case:
         return run_case(args.case, args.case_precision, args.case_steps)
+    if args.cpu_sample:
+        print(json.dumps(cpu_baseline(args.cpu_sample, args.cpu_steps)))
+        return 0
 
     import numpy as np
     import torch
@@ -437,28 +457,27 @@ def main():
     ms_mixed, ms_fp64 = aggregate(ws, [ms_mixed, ms_fp64], dist if ws > 1 else None, dev)
     clk = clocks.stop()
 
-    # mixed vs FP64 after the same number of steps (warmup + steps for each)
-    l1 = None
-    if args.steps + args.warmup == steps64 + args.warmup:
-        l1 = float((rho_mixed - rho_fp64).abs().mean())
-    else:
-        # equal-step comparison on a separate short run
-        s1 = B.Solver((N, N), bc=B.BC_PERIODIC, precision=1)
-        s0 = B.Solver((N, N), bc=B.BC_PERIODIC, precision=0)
-        Wd1, Gd1 = torch.from_numpy(W).to(dev), torch.from_numpy(G).to(dev)
-        Wd0, Gd0 = Wd1.clone(), Gd1.clone()
-        s1.set_state(Wd1, Gd1)
-        s0.set_state(Wd0, Gd0)
-        for _ in range(steps64 + args.warmup):
-            dt = CFL * h / s0.max_wavespeed()
-            s0.step(dt)
-            s1.step(dt)
-        s1.get_state(Wd1, Gd1)
-        s0.get_state(Wd0, Gd0)
-        l1 = float((Wd1[0] - Wd0[0]).abs().mean())
-        l1_steps = steps64 + args.warmup
-        s1.close()
-        s0.close()
+    # mixed vs FP64 on the same 100 CFL steps (the FP64 path's time steps
+    # drive both), density L1 and L-inf
+    L1_STEPS = 100
+    s1 = B.Solver((N, N), bc=B.BC_PERIODIC, precision=1)
+    s0 = B.Solver((N, N), bc=B.BC_PERIODIC, precision=0)
+    Wd1, Gd1 = torch.from_numpy(W).to(dev), torch.from_numpy(G).to(dev)
+    Wd0, Gd0 = Wd1.clone(), Gd1.clone()
+    s1.set_state(Wd1, Gd1)
+    s0.set_state(Wd0, Gd0)
+    for _ in range(L1_STEPS):
+        dt = CFL * h / s0.max_wavespeed()
+        s0.step(dt)
+        s1.step(dt)
+    s1.get_state(Wd1, Gd1)
+    s0.get_state(Wd0, Gd0)
+    drho = (Wd1[0] - Wd0[0]).abs()
+    l1, linf = float(drho.mean()), float(drho.max())
+    st_l1 = [s1.status(), s0.status()]
+    s1.close()
+    s0.close()
+    del Wd1, Gd1, Wd0, Gd0
 
     e2e_val, h2d, d2h = time_e2e(B, torch, W, G, 1, max(2, min(args.steps, 5)), 1, dev)
     batch = time_batch(B, torch, max(3, min(args.steps, 20)), dev) if not args.headline_only else None
@@ -493,6 +512,8 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+        one = cpu_single_core()
+        cpu["single_core"] = {"value": one["value"], "unit": one["unit"], "cores": one["cores"], "sample": one["sample"]}
 
     line = {
         "metric": METRIC,
@@ -518,6 +539,8 @@ def main():
                  "roofline": {"bound": "alu", "achieved": achieved64, "peak": fp64_peak, "unit": "TFLOP/s",
                               "frac": achieved64 / fp64_peak, "traffic": TRAFFIC_PER_FLUX_LAUNCH["fp64"]}},
         "l1_density_mixed_vs_fp64": l1,
+        "linf_density_mixed_vs_fp64": linf,
+        "error_steps": L1_STEPS,
         "hbm_roofline_frac": hbm_frac,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": TRAFFIC_PER_FLUX_LAUNCH["mixed"],
@@ -525,7 +548,7 @@ def main():
                      "peak_source": "FP32: SMs x 128 lanes x 2 flop x max SM clock"},
         "kernel_ms": {name: prof_mixed[k][1] / max(prof_mixed[k][0], 1) for k, name in
                       ((B.KC_RECON, "cell_poly"), (B.KC_FACE, "face_flux"), (B.KC_UPDATE, "update"), (B.KC_DT, "dt"))},
-        "status": {"mixed": st_mixed, "fp64": st_fp64},
+        "status": {"mixed": st_mixed, "fp64": st_fp64, "error_run": st_l1},
         "e2e": {"value": ws * e2e_val, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "batched_256_grids": batch,
