@@ -81,6 +81,38 @@ def test_reconstruct_parity(dim, n, bc):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fallback_states_parity(precision):
+    """The admissibility fallback in both branches: the oracle tests' state
+    where every candidate polynomial carries the same steep slope, at
+    thresholds 0.3 and 0.6 (about a thousand replaced states each, and the
+    kept states' margins of at least 10% decide alike in FP32).  The GPU
+    replaces exactly the states the oracle does, and the values agree
+    element-wise (FP64: 1e-12 of the scale; mixed: FP32 rounding)."""
+    from test_oracle_admissibility import _steep_gradient
+
+    n = (24, 20)
+    W, G, h = _steep_gradient(n)
+    for delta in (0.3, 0.6):
+        ref = O.reconstruct(O.make_cfg(2, n, h, bc=0, adm_delta=delta), W, G)
+        s = _solver(2, n, h, 0, precision=precision, adm_delta=delta)
+        s.set_state(_dev(W), _dev(G))
+        out = torch.zeros(ref.size, dtype=torch.float64, device=DEV)
+        s.reconstruct(out)
+        got = out.cpu().numpy().reshape(ref.shape)
+        s.close()
+        # replaced states: zero slopes in every variable
+        ref_fb = np.all(ref[:, :, 1:] == 0.0, axis=(1, 2))
+        got_fb = np.all(got[:, :, 1:] == 0.0, axis=(1, 2))
+        assert ref_fb.sum() >= 1000 and np.array_equal(got_fb, ref_fb)
+        tol = 1e-12 if precision == 0 else 2e-6
+        for v in range(4):
+            scale = np.abs(W[v]).max()
+            np.testing.assert_allclose(got[:, v, 0], ref[:, v, 0], rtol=0, atol=tol * scale)
+            dscale = np.abs(ref[:, v, 1:]).max() + scale / h
+            np.testing.assert_allclose(got[:, v, 1:], ref[:, v, 1:], rtol=0, atol=10 * tol * dscale)
+
+
 @pytest.mark.parametrize("dim,n", CASES)
 def test_flux_parity(dim, n):
     bc = 1
