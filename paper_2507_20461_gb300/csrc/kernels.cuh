@@ -844,20 +844,20 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
                 ff[(long)(2 * NV + v) * nft + face] = Wh[fv];
             }
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        int fv = v;
-        if (v >= 1 && v <= M) {
+        for (int v = 0; v < NV; ++v) {
+            int fv = v;
+            if (v >= 1 && v <= M) {
 #pragma unroll
-            for (int kk = 0; kk < M; ++kk)
-                if (ax[kk] == v - 1) fv = 1 + kk;
+                for (int kk = 0; kk < M; ++kk)
+                    if (ax[kk] == v - 1) fv = 1 + kk;
+            }
+            if (!valid) continue;
+            ff[((long)(0 * NV + v) * NG + g) * nft + face] = F[fv];
+            ff[((long)(1 * NV + v) * NG + g) * nft + face] = Ft[fv];
+            ff[((long)(2 * NV + v) * NG + g) * nft + face] = Wh[fv];
         }
-        if (!valid) continue;
-        ff[((long)(0 * NV + v) * NG + g) * nft + face] = F[fv];
-        ff[((long)(1 * NV + v) * NG + g) * nft + face] = Ft[fv];
-        ff[((long)(2 * NV + v) * NG + g) * nft + face] = Wh[fv];
     }
 }
 
