@@ -914,7 +914,7 @@ static int recon_all(const or_cfg *c, const double *W, const double *G, double *
             /* face f lies between cells f-1 and f; left reconstruction cell f-1 */
             for (int side = 0; side < 2; ++side) {
                 int rc = side ? f : f - 1;
-                double val[5], der[5], wc[5];
+                double val[5] = {0}, der[5] = {0}, wc[5] = {0};
                 for (int v = 0; v < nv; ++v) {
                     double w5[5], d5[5];
                     for (int q = -2; q <= 2; ++q) {
@@ -1160,7 +1160,7 @@ static int nc_states(const or_cfg *c, int order, const double *W, double *st)
             fetch(c, W, Gz, (int)f + 2 - i, 0, 0, w6[1][i], g); /* mirrored: cell f at i = 2 */
         }
         for (int side = 0; side < 2; ++side) {
-            double s3[3];
+            double s3[3] = {0};
             for (int v = 0; v < nv; ++v) {
                 long double u[6], val;
                 for (int i = 0; i < 6; ++i) u[i] = w6[side][i][v];
