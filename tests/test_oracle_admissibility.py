@@ -14,9 +14,6 @@ code:
   delta only adds fallbacks.
 """
 import numpy as np
-import pytest
-
-from paper_2507_20461_gb300 import inputs as I
 
 GAMMA = 1.4
 
