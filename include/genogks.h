@@ -210,7 +210,12 @@ int gks_status(gks_handle_t h);
 #define GKS_KC_FACE 1
 #define GKS_KC_UPDATE 2
 #define GKS_KC_DT 3
+/* on != 0 starts (0 stops) the bracketing; reset != 0 zeroes the counts.
+ * GKS_ERR_ARG for a NULL handle, GKS_ERR_OOM / GKS_ERR_CUDA if the events
+ * cannot be created. */
 int gks_profile_enable(gks_handle_t h, int on, int reset);
+/* launches and ms may be NULL (that output is skipped).  GKS_ERR_ARG for a
+ * NULL handle or a class outside 0..7. */
 int gks_profile_read(gks_handle_t h, int kernel_class, long *launches, double *ms);
 
 /* Free everything the handle owns (not a caller workspace).  NULL is a no-op. */
@@ -314,7 +319,10 @@ const char *gks_batch_tuning(gks_batch_t b);
 /* Synchronise and return the status word (as gks_status). */
 int gks_batch_status(gks_batch_t b);
 
+/* Wait for the batch's work and free everything it owns.  NULL is a no-op. */
 int gks_batch_destroy(gks_batch_t b);
+/* Message of the last error on this batch ("" if none); b == NULL gives the
+ * last create error of this thread.  Owned by the library. */
 const char *gks_batch_last_error(gks_batch_t b);
 
 #ifdef __cplusplus
