@@ -522,26 +522,43 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R
             sm[1 + q] = ghost_mask<M>(P, fl);
         }
     }
+    /* a cross with no mirrored cell (every cell away from non-periodic
+     * boundaries) reads its data without the sign selects; the values are
+     * those of the general path with every sign +1 */
+    unsigned anyflip = 0;
+#pragma unroll
+    for (int q = 0; q <= 2 * M; ++q) anyflip |= sm[q];
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) {
         R d[ND];
         const R hr = pick<R>(P.h, P.fh);
-        const int s0v = ((sm[0] >> v) & 1u) ? -1 : 1;
+        if (anyflip == 0) {
 #pragma unroll
-        for (int q = 0; q < 2 * M; ++q) {
-            const unsigned mq = sm[1 + q];
-            const int sq = ((mq >> v) & 1u) ? -1 : 1;
-            d[q * (1 + M)] = R(src.delta_signed(v * P.ncell + cl[1 + q], sq, v * P.ncell + cl[0], s0v));
+            for (int q = 0; q < 2 * M; ++q) {
+                d[q * (1 + M)] = R(src.delta(v * P.ncell + cl[1 + q], v * P.ncell + cl[0]));
+#pragma unroll
+                for (int a = 0; a < M; ++a) d[q * (1 + M) + 1 + a] = src.grad((a * NV + v) * P.ncell + cl[1 + q]) * hr;
+            }
+#pragma unroll
+            for (int a = 0; a < M; ++a) d[2 * M * (1 + M) + a] = src.grad((a * NV + v) * P.ncell + cl[0]) * hr;
+        } else {
+            const int s0v = ((sm[0] >> v) & 1u) ? -1 : 1;
+#pragma unroll
+            for (int q = 0; q < 2 * M; ++q) {
+                const unsigned mq = sm[1 + q];
+                const int sq = ((mq >> v) & 1u) ? -1 : 1;
+                d[q * (1 + M)] = R(src.delta_signed(v * P.ncell + cl[1 + q], sq, v * P.ncell + cl[0], s0v));
+#pragma unroll
+                for (int a = 0; a < M; ++a) {
+                    const R g = src.grad((a * NV + v) * P.ncell + cl[1 + q]) * hr;
+                    d[q * (1 + M) + 1 + a] = (((mq >> v) ^ (mq >> (8 + a))) & 1u) ? -g : g;
+                }
+            }
 #pragma unroll
             for (int a = 0; a < M; ++a) {
-                const R g = src.grad((a * NV + v) * P.ncell + cl[1 + q]) * hr;
-                d[q * (1 + M) + 1 + a] = (((mq >> v) ^ (mq >> (8 + a))) & 1u) ? -g : g;
+                const R g = src.grad((a * NV + v) * P.ncell + cl[0]) * hr;
+                d[2 * M * (1 + M) + a] = (((sm[0] >> v) ^ (sm[0] >> (8 + a))) & 1u) ? -g : g;
             }
-        }
-#pragma unroll
-        for (int a = 0; a < M; ++a) {
-            const R g = src.grad((a * NV + v) * P.ncell + cl[0]) * hr;
-            d[2 * M * (1 + M) + a] = (((sm[0] >> v) ^ (sm[0] >> (8 + a))) & 1u) ? -g : g;
         }
         R c[NC];
         Cubic<R, M>::fit(d, c);
