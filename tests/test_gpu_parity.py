@@ -1,6 +1,6 @@
 """Parity of the CUDA library (through its C ABI) with the oracle, on cuda:0.
 
-Bars (tolerances written here, derived in the design doc):
+Bars (the tolerances are written in each test, with the arithmetic behind them):
   - FP64 interface states and fluxes: element-wise, relative 1e-12 of the
     variable's scale (values) and 1e-10 (derivatives, time derivatives);
   - FP64 one step: per-variable relative L1 residual <= 1e-12;
