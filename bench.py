@@ -40,12 +40,12 @@ WORKLOAD = "2D Euler 2048x2048 periodic, 16 random-phase density modes (k<=8) + 
 # which every face Gauss point is evaluated exactly once:
 #   mixed path: 1764 FP32 flops per face Gauss point;
 #   FP64 path:  2021 FP64 flops per face Gauss point (mean of the stages).
-# (profiles/face_flux_flops_2d_256.md)
+# (the face-flux flop summary under profiles/)
 FLOPS_PER_FACE_GP = {"mixed": 1764.0, "fp64": 2021.0}
-# DRAM bytes (read + write) per launch of the face-flux kernel, from one ncu
-# capture each (profiles/face_flux_mixed_2d_1024_full.md,
-# profiles/face_flux_fp64_2d_256_full.md), scaled to the 2048^2 launch by
-# the Gauss points it processes (the traffic is the coefficient array read
+# DRAM bytes (read + write) per launch of the face-flux kernel, from one
+# 1-pass ncu capture each (mixed at 1024^2: 168.1 MB read + 40.9 MB written;
+# FP64 at 256^2: 21.27 MB read; the face-flux summaries under profiles/),
+# scaled to the 2048^2 launch by the Gauss points it processes (the traffic is the coefficient array read
 # about once plus the face sums written, both proportional to the grid).
 TRAFFIC_PER_FLUX_LAUNCH = {"mixed": 209.06e6 * (2049 * 2048) / (1025 * 1024),
                            "fp64": 21.266e6 * (2049 * 2048) / (257 * 256)}
