@@ -5,7 +5,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, FP64 restatement of
  * the method, used by the test-suite, the smoke check and the CPU baseline of
- * the benchmark to judge the CUDA library.  The product path never calls it.
+ * the benchmark to check the CUDA library.  The product path never calls it.
  * It shares no code, header, table or constant with the CUDA library.
  *
  * Everything is written the direct way:

@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(128, (flux_blocks_per_sm<R, M, NS>())) face_fl
 
 /* Shared-memory carveout of a kernel with static shared memory: the smallest
  * share of the SM's unified L1/shared storage that still holds `blocks`
- * resident blocks (the driver rounds the preference up to the next supported
+ * resident blocks (the CUDA driver rounds the preference up to the next supported
  * capacity; the default can hold fewer blocks than the launch bounds ask
  * for), so the rest stays L1.  Set once per kernel; a refusal leaves the
  * default. */
