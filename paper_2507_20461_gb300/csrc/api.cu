@@ -325,9 +325,11 @@ int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const
         off += f;
     }
     P.nftot = off;
-    /* the kernels decompose indices in 32-bit arithmetic */
+    /* the kernels decompose indices in 32-bit arithmetic; the FP32 flux
+     * rounds its (face, Gauss point) index space up to whole 128-item groups */
     bool fits = next < (1L << 32) && ncell < (1L << 32);
-    for (int d = 0; d < grid->dim; ++d) fits = fits && P.nface[d] * gks::ngauss(grid->dim) < (1L << 32);
+    for (int d = 0; d < grid->dim; ++d)
+        fits = fits && (P.nface[d] * gks::ngauss(grid->dim) + 127) / 128 * 128 < (1L << 32);
     if (!fits) {
         if (c->own_ws) cudaFree(c->ws);
         delete c;

@@ -269,9 +269,17 @@ int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs,
         return bfail(nullptr, GKS_ERR_ARG, "ao_d0 and teno_ct must lie in (0, 1)");
     if (o.workspace) return bfail(nullptr, GKS_ERR_UNSUPPORTED, "batched mode allocates its own workspace");
     if (o.mu != 0.0) return bfail(nullptr, GKS_ERR_UNSUPPORTED, "batched mode solves the Euler equations only (mu = 0)");
-    for (int g = 0; g < nbatch; ++g)
+    for (int g = 0; g < nbatch; ++g) {
         if (nx[g] < 1 || ny[g] < 1 || nx[g] > (1 << 20) || ny[g] > (1 << 20) || !(hs[g] > 0.0))
             return bfail(nullptr, GKS_ERR_ARG, "grid %d: invalid size or cell size", g);
+        /* the kernels decompose indices in 32-bit arithmetic; the flux's
+         * (face, Gauss point) index space is rounded up to 128-item groups */
+        const long ext = (long)(nx[g] + 2) * (ny[g] + 2);
+        const long gx = ((long)(nx[g] + 1) * ny[g] * 2 + 127) / 128 * 128;
+        const long gy = ((long)nx[g] * (ny[g] + 1) * 2 + 127) / 128 * 128;
+        if (ext >= (1L << 32) || gx >= (1L << 32) || gy >= (1L << 32))
+            return bfail(nullptr, GKS_ERR_UNSUPPORTED, "grid %d too large (an index space reaches 2^32)", g);
+    }
 
     gks_batch_ctx *b = new (std::nothrow) gks_batch_ctx();
     if (!b) return bfail(nullptr, GKS_ERR_OOM, "host allocation");
