@@ -9,8 +9,8 @@ P4  design order on the advected density sine wave (Sec. 6.1, Sec. 6.10):
 P5  conservation: with periodic boundaries the sums of the cell averages are
     constant (Eq. semifvs, telescoping fluxes); the sums of the cell-averaged
     gradients vanish (Eq. slope, telescoping interface states).
-P8  symmetries: mirror x -> -x, transposition x <-> y, and invariance of
-    y-independent data.
+P8  symmetries: mirror x -> -x, transposition x <-> y, the 3D axis cycle
+    x -> y -> z -> x, and invariance of y-independent data.
 P9  convergence to the exact Riemann solution of seeded two-state problems.
 """
 import math
@@ -144,6 +144,44 @@ def test_transpose_symmetry_2d(oracle):
     W2b, G2b = transpose(W2, G2)
     np.testing.assert_allclose(W2b, W1, rtol=1e-12, atol=1e-13)
     np.testing.assert_allclose(G2b, G1, rtol=1e-10, atol=1e-10)
+
+
+def test_axis_cycle_symmetry_3d(oracle):
+    """The rotation x' = y, y' = z, z' = x: on a non-cubic grid with data
+    varying in every component, stepping the rotated state and rotating back
+    gives the original run (the face frames' transverse axes, the tangential
+    slopes and the transverse moments must follow the axes)."""
+    rng = np.random.default_rng(6)
+    nx, ny, nz = 6, 7, 8
+    h = 1.0 / nx
+    shape = (nz, ny, nx)
+    rho = 1.0 + 0.2 * rng.random(shape)
+    vel = [0.3 * (rng.random(shape) - 0.5) for _ in range(3)]
+    p = 1.0 + 0.2 * rng.random(shape)
+    ke = sum(u * u for u in vel)
+    W = np.stack([rho] + [rho * u for u in vel] + [p / 0.4 + 0.5 * rho * ke])
+    G = 0.3 * rng.normal(size=(3,) + W.shape)
+
+    def cycle(W, G):
+        """new [v][z'][y'][x'] = old [v][x][z][y]; u' = v, v' = w, w' = u;
+        d/dx' = d/dy, d/dy' = d/dz, d/dz' = d/dx"""
+        Wc = np.transpose(W, (0, 3, 1, 2))[[0, 2, 3, 1, 4]].copy()
+        Gc = np.transpose(G, (0, 1, 4, 2, 3))[:, [0, 2, 3, 1, 4]][[1, 2, 0]].copy()
+        return Wc, Gc
+
+    dt = 0.05 * h
+    W1, G1 = _run(oracle, oracle.make_cfg(3, (nx, ny, nz), h, bc=1), W, G, dt, 2)
+    Wc, Gc = cycle(W, G)
+    W2, G2 = _run(oracle, oracle.make_cfg(3, (ny, nz, nx), h, bc=1), Wc, Gc, dt, 2)
+    W2b, G2b = cycle(*cycle(W2, G2))
+    np.testing.assert_allclose(W2b, W1, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(G2b, G1, rtol=1e-10, atol=1e-10)
+    # not vacuous: rotating the axes but not the momentum components breaks it
+    Wx = np.transpose(W, (0, 3, 1, 2)).copy()
+    Gx = np.transpose(G, (0, 1, 4, 2, 3))[[1, 2, 0]].copy()
+    W3, G3 = _run(oracle, oracle.make_cfg(3, (ny, nz, nx), h, bc=1), Wx, Gx, dt, 2)
+    W3b = np.transpose(W3, (0, 2, 3, 1))
+    assert np.abs(W3b[[0, 4]] - W1[[0, 4]]).max() > 1e-6
 
 
 def test_y_invariant_stays_y_invariant(oracle):
