@@ -210,10 +210,10 @@ def run_reference(args):
     return 0
 
 
-def time_path(B, torch, W, G, h, precision, steps, warmup, dev):
+def time_path(B, torch, W, G, h, precision, steps, warmup, dev, limiter=0):
     """Device-timed steps of one precision; returns (ms/step, profile, final density)."""
     stream = torch.cuda.current_stream()
-    s = B.Solver((N, N), bc=B.BC_PERIODIC, precision=precision, stream=stream)
+    s = B.Solver((N, N), bc=B.BC_PERIODIC, precision=precision, stream=stream, limiter=limiter)
     Wd = torch.from_numpy(W).to(dev)
     Gd = torch.from_numpy(G).to(dev)
     s.set_state(Wd, Gd)
@@ -234,6 +234,72 @@ def time_path(B, torch, W, G, h, precision, steps, warmup, dev):
     rho = Wd[0].clone()
     s.close()
     return ms, prof, rho, st
+
+
+def time_limiters(B, torch, W, G, h, steps, warmup, dev, ms_geno):
+    """The WENO-Z and TENO weight variants (limiter 2, 3) on the headline
+    workload, mixed precision, through the same timed path: they change only
+    the per-cell reconstruction, so the face flux (the roofline kernel) is the
+    headline's."""
+    out = {"workload": "2D 2048^2 headline workload, mixed precision, limiter 2 (WENO-Z) / 3 (TENO)"}
+    for name, lim in (("weno_z", 2), ("teno", 3)):
+        ms, prof, _, st = time_path(B, torch, W, G, h, 1, steps, warmup, dev, limiter=lim)
+        out[name] = {
+            "value": N * N / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps, "status": st,
+            "vs_geno_ms": ms / ms_geno,
+            "kernel_ms": {nm: prof[k][1] / max(prof[k][0], 1) for k, nm in
+                          ((B.KC_RECON, "cell_poly"), (B.KC_FACE, "face_flux"), (B.KC_UPDATE, "update"))},
+        }
+    return out
+
+
+def time_noncompact(B, torch, steps, dev):
+    """The 1D non-compact GENO schemes (order 5 and 6, HLLC flux, classical
+    RK4; FP64) on 2^22 cells of the config-1 family (seeded two-state Riemann
+    problem, transmissive), through gks_step_cfl.  Throughput and the split
+    between the face kernel (reconstruction + HLLC) and the RK4 update."""
+    import numpy as np
+
+    from paper_2507_20461_gb300 import inputs as I
+
+    n = 1 << 22
+    W, G, h, _ = I.riemann_1d(n, seed=20461)
+    out = {"workload": f"1D {n} cells, two-state Riemann IC (rho, p ~ U[0.1,1], u ~ U[-0.5,0.5]), transmissive, "
+                       "CFL 0.4, FP64, one classical RK4 step per step"}
+    stream = torch.cuda.current_stream()
+    for order in (5, 6):
+        s = B.Solver((n,), lo=[0.0], hi=[n * h], bc=B.BC_TRANSMISSIVE, precision=0, order=order, stream=stream)
+        Wd = torch.from_numpy(np.ascontiguousarray(W)).to(dev)
+        Gd = torch.from_numpy(np.ascontiguousarray(G)).to(dev)
+        s.set_state(Wd, Gd)
+        s.step_cfl(CFL, 2)
+        torch.cuda.synchronize()
+        s.profile(True, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step_cfl(CFL, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = {k: s.profile_read(k) for k in (B.KC_FACE, B.KC_UPDATE)}
+        s.profile(False, False)
+        st = s.status()
+        s.close()
+        out[f"order{order}"] = {
+            "value": n / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps, "status": st,
+            "kernel_ms_per_step": {"faces": prof[B.KC_FACE][1] / steps, "rk4_update": prof[B.KC_UPDATE][1] / steps},
+        }
+    return out
+
+
+def _guarded(fn, *a):
+    """A secondary measurement: an exception becomes an error entry and
+    leaves the rest of the line intact."""
+    try:
+        return fn(*a)
+    except Exception as ex:  # noqa: BLE001
+        return {"error": f"{type(ex).__name__}: {ex}"[:300]}
 
 
 def time_e2e(B, torch, W, G, precision, steps, warmup, dev):
@@ -495,6 +561,9 @@ def main():
     batch = time_batch(B, torch, max(3, min(args.steps, 20)), dev) if not args.headline_only else None
     three_d = time_3d(B, torch, max(3, min(args.steps, 10)), dev) if not args.headline_only else None
     tgv = time_tgv(B, torch, max(3, min(args.steps, 10)), dev) if not args.headline_only else None
+    limiters = None if args.headline_only else _guarded(
+        time_limiters, B, torch, W, G, h, max(3, min(args.steps, 10)), args.warmup, dev, ms_mixed)
+    noncompact = None if args.headline_only else _guarded(time_noncompact, B, torch, max(3, min(args.steps, 10)), dev)
 
     peaks, peak_src = _peaks()
     sm_clock = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
@@ -567,6 +636,8 @@ def main():
         "batched_256_grids": batch,
         "three_d_256": three_d,
         "navier_stokes_tgv_256": tgv,
+        "limiter_variants_2048": limiters,
+        "noncompact_1d": noncompact,
         "clocks": clk,
         "cpu_baseline": cpu,
         "peaks_source": peak_src,
