@@ -55,7 +55,8 @@ extern "C" {
 #define GKS_ERR_CUDA (-2)        /* a CUDA call failed (message in gks_last_error)           */
 #define GKS_ERR_OOM (-3)         /* device allocation failed or workspace too small          */
 #define GKS_ERR_NONPHYSICAL (-4) /* rho <= 0, p <= 0 or a non-finite value was produced      */
-#define GKS_ERR_TIMEOUT (-5)     /* a bounded device wait gave up                            */
+/* (-5) is not used: no kernel of this library waits on another block or
+ * on the host, so no device wait can time out */
 #define GKS_ERR_UNSUPPORTED (-6) /* combination not provided (e.g. order 8 in 2D)           */
 
 /* Status-word bits (gks_status): which condition was seen by the device. */
@@ -248,13 +249,15 @@ const char *gks_last_error(gks_handle_t h);
  * library holds until the process exits, which limits the grid to
  * (nx + 2) * (ny + 2) <= 14400 cells including the one-cell ghost ring (for
  * example 118 x 118); larger grids return
- * GKS_ERR_ARG, as do invalid sizes, gamma, bc, dt or NULL pointers.
+ * GKS_ERR_ARG, as do invalid sizes, h, gamma, bc, dt, NULL pointers and the
+ * scheme constants geno_gks_create rejects.
  * GKS_ERR_UNSUPPORTED: precision != 0 or mu != 0 (Euler flux only).
  * GKS_ERR_NONPHYSICAL: a face state the
  * flux could not use.  GKS_ERR_CUDA: a CUDA call failed.
  *
  * The first call on a device looks up the device address of that array
- * (with the device current); make that first call before any stream capture.
+ * (with the device current).  Every call copies the status word to the host
+ * and synchronises `stream` before it returns.
  * Every call on a device shares the array and leaves its contents behind;
  * calls that overlap on the GPU (other streams or unordered host threads)
  * race on it and must be serialised by the caller. */

@@ -15,7 +15,7 @@ import numpy as np
 from . import _build
 
 OK = 0
-ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONPHYSICAL, ERR_UNSUPPORTED = -1, -2, -3, -4, -6
 ST_RHO, ST_P, ST_NAN, ST_FLUX = 1, 2, 4, 8
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_NOSLIP = 0, 1, 2, 3
 LIMITER_GENO, LIMITER_LINEAR, LIMITER_WENOZ, LIMITER_TENO = 0, 1, 2, 3

@@ -57,9 +57,11 @@ int scratch_address(unsigned char **out)
 extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc_t bc, const gks_opts_t *opts,
                                   const double *W, const double *G, double dt, double *face_flux, void *stream)
 {
-    if (nx < 1 || ny < 1 || !(h > 0.0) || !(gamma > 1.0)) return GKS_ERR_ARG;
-    /* larger grids do not fit the static scratch */
-    if ((long)(nx + 2) * (ny + 2) > kMaxExtCells) return GKS_ERR_ARG;
+    if (nx < 1 || ny < 1 || !(h > 0.0) || !std::isfinite(h) || !(gamma > 1.0) || !std::isfinite(gamma))
+        return GKS_ERR_ARG;
+    /* larger grids do not fit the static scratch (widened before adding, so
+     * sides near INT_MAX cannot wrap) */
+    if (((long)nx + 2) * ((long)ny + 2) > kMaxExtCells) return GKS_ERR_ARG;
     if (bc != GKS_BC_PERIODIC && bc != GKS_BC_TRANSMISSIVE && bc != GKS_BC_REFLECTIVE && bc != GKS_BC_NOSLIP)
         return GKS_ERR_ARG;
     if (!W || !G || !face_flux) return GKS_ERR_ARG;
@@ -70,6 +72,11 @@ extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc
     if (o.precision != 0 || o.mu != 0.0) return GKS_ERR_UNSUPPORTED;
     if (o.limiter < 0 || o.limiter > 3) return GKS_ERR_ARG;
     if (o.limiter >= 2 && (!(o.ao_d0 > 0.0) || !(o.ao_d0 < 1.0) || !(o.teno_ct > 0.0) || !(o.teno_ct < 1.0)))
+        return GKS_ERR_ARG;
+    /* the scheme constants geno_gks_create accepts, and no others */
+    if (!(o.C > 0.0) || !(o.eps > 0.0) || !(o.C0 > 0.0) || !(o.c1_tau >= 0.0) || !(o.c2_tau >= 0.0) ||
+        !(o.adm_delta >= 0.0) || !(o.adm_delta < 1.0) || !std::isfinite(o.C) || !std::isfinite(o.C0) ||
+        !std::isfinite(o.c1_tau) || !std::isfinite(o.c2_tau))
         return GKS_ERR_ARG;
 
     unsigned char *base = nullptr;
@@ -116,6 +123,8 @@ extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc
     if (e == cudaSuccess) {
         gks::set_scalar_kernel<<<1, 1, 0, s>>>(dtp, dt);
         const gks::Src<double> src{W, G};
+        gks::face_flux_prepare<double, 2, 0, true>();
+        gks::face_flux_prepare<double, 2, 1, true>();
         gks::cell_poly_kernel<double, 2><<<gks::blocks_for(P.next), gks::kBlock, 0, s>>>(P, src, B);
         gks::face_flux_kernel<double, 2, 0, true>
             <<<gks::blocks_for(P.nface[0] * 2), gks::kBlock, 0, s>>>(P, src, B, dtp, nullptr, face_flux, status);

@@ -98,3 +98,43 @@ def test_fast_division_formula():
         for n in ns:
             if 0 <= n < 2**32:
                 assert (M * n) >> 64 == n // d, (d, n)
+
+
+def _static_flux():
+    f = B.lib().gks_flux_2d_static
+    f.restype = C.c_int
+    f.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p,
+                  C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
+    return f
+
+
+def _bad_opts(**kw):
+    o = B.default_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@pytest.mark.parametrize(
+    "nx,ny,h,opts",
+    [
+        (2**31 - 2, 10, 0.1, None),     # (nx + 2) wraps in 32-bit arithmetic
+        (10, 2**31 - 2, 0.1, None),
+        (2**31 - 1, 2**31 - 1, 0.1, None),
+        (200, 200, 0.005, None),        # beyond the static scratch
+        (10, 10, float("inf"), None),
+        (10, 10, 0.1, dict(C=0.0)),     # 1 / tanh(0)
+        (10, 10, 0.1, dict(eps=0.0)),
+        (10, 10, 0.1, dict(C0=-1.0)),
+        (10, 10, 0.1, dict(c1_tau=-0.1)),
+        (10, 10, 0.1, dict(adm_delta=1.0)),
+    ],
+)
+def test_static_flux_rejects_before_any_launch(nx, ny, h, opts):
+    """gks_flux_2d_static turns sizes and constants it cannot use into
+    GKS_ERR_ARG on the host, before it touches a GPU (so this runs without
+    one); the pointers are never dereferenced."""
+    o = C.byref(_bad_opts(**opts)) if opts else None
+    p = C.c_void_p(256)
+    r = _static_flux()(nx, ny, h, 1.4, B.BC_PERIODIC, o, p, p, 1e-3, p, None)
+    assert r == B.ERR_ARG

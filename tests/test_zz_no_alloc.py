@@ -34,13 +34,19 @@ def _state(nx, ny, seed):
     return W, G, h
 
 
-def _reference(nx, ny, h, bc, W, G, dt):
-    s = B.Solver((nx, ny), lo=[0, 0], hi=[nx * h, ny * h], bc=bc, precision=0)
+def _reference(nx, ny, h, bc, W, G, dt, limiter=0):
+    s = B.Solver((nx, ny), lo=[0, 0], hi=[nx * h, ny * h], bc=bc, precision=0, limiter=limiter)
     s.set_state(torch.from_numpy(W).to(DEV), torch.from_numpy(G).to(DEV))
     out = torch.zeros(3 * 4 * 2 * s.nfaces, dtype=torch.float64, device=DEV)
     s.flux(dt, out)
     s.close()
     return out.cpu().numpy()
+
+
+def _opts(limiter):
+    o = B.default_opts()
+    o.limiter = limiter
+    return o
 
 
 def test_static_flux_matches_gks_flux_twice():
@@ -67,3 +73,46 @@ def test_static_flux_rejects_oversized_grid():
     out = torch.zeros(10, dtype=torch.float64, device=DEV)
     r = f(200, 200, 0.005, 1.4, B.BC_PERIODIC, None, W.data_ptr(), G.data_ptr(), 1e-3, out.data_ptr(), None)
     assert r == B.ERR_ARG
+
+
+@pytest.mark.parametrize("bc,limiter", [(B.BC_REFLECTIVE, 0), (B.BC_NOSLIP, 0), (B.BC_TRANSMISSIVE, 2),
+                                        (B.BC_PERIODIC, 3)])
+def test_static_flux_walls_and_weight_variants(bc, limiter):
+    """Slip and no-slip walls (mirrored ghosts with sign flips) and the
+    WENO-Z / TENO weights go through the same kernels as gks_flux."""
+    f = _static_fn()
+    stream = torch.cuda.current_stream().cuda_stream
+    nx, ny, dt = 33, 27, 0.0015
+    W, G, h = _state(nx, ny, 11 + limiter + 3 * bc)
+    ref = _reference(nx, ny, h, bc, W, G, dt, limiter)
+    o = _opts(limiter)
+    for _ in range(2):
+        out = torch.full((ref.size,), float("nan"), dtype=torch.float64, device=DEV)
+        r = f(nx, ny, h, 1.4, bc, C.byref(o), torch.from_numpy(W).to(DEV).data_ptr(),
+              torch.from_numpy(G).to(DEV).data_ptr(), dt, out.data_ptr(), stream)
+        assert r == B.OK
+        got = out.cpu().numpy()
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_static_flux_reports_a_nonphysical_state():
+    """A block of cells at negative pressure leaves face states the flux
+    cannot use: the call says so, and a later valid call is unaffected (the
+    status word is cleared per call)."""
+    f = _static_fn()
+    stream = torch.cuda.current_stream().cuda_stream
+    nx, ny, dt = 20, 16, 0.002
+    W, G, h = _state(nx, ny, 5)
+    Wbad = W.copy()
+    # E below the kinetic energy: p < 0 in a 3 x 3 block
+    ke = 0.5 * (Wbad[1] ** 2 + Wbad[2] ** 2) / Wbad[0]
+    Wbad[3, 6:9, 8:11] = ke[6:9, 8:11] - 1.0
+    out = torch.zeros(3 * 4 * 2 * ((nx + 1) * ny + nx * (ny + 1)), dtype=torch.float64, device=DEV)
+    r = f(nx, ny, h, 1.4, B.BC_PERIODIC, None, torch.from_numpy(Wbad).to(DEV).data_ptr(),
+          torch.from_numpy(G).to(DEV).data_ptr(), dt, out.data_ptr(), stream)
+    assert r == B.ERR_NONPHYSICAL
+    ref = _reference(nx, ny, h, B.BC_PERIODIC, W, G, dt)
+    r = f(nx, ny, h, 1.4, B.BC_PERIODIC, None, torch.from_numpy(W).to(DEV).data_ptr(),
+          torch.from_numpy(G).to(DEV).data_ptr(), dt, out.data_ptr(), stream)
+    assert r == B.OK
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
