@@ -114,6 +114,15 @@ typedef struct {
                          candidate; the sub-stencils share 1 - d0 (0.85)         */
     double teno_ct;   /* limiter 3: cut-off C_T (1e-6; the paper uses 1e-3 for
                          the Titarev-Toro problem), Sec. 5.1                     */
+    int stage_kernels; /* how a 2D mixed-precision stage runs (gks_step,
+                         gks_step_cfl): 0 = three kernels (per-cell
+                         reconstruction, per-direction face flux, update) with
+                         the blended cubics and face sums in device memory;
+                         1 = one fused kernel per stage (reconstruction, flux
+                         and update of a strip swept row by row in shared
+                         memory).  Both give the same result to FP32 rounding.
+                         Other precisions and dimensions always use the
+                         three-kernel path (0)                                   */
 } gks_opts_t;
 
 typedef struct gks_ctx *gks_handle_t;
@@ -206,11 +215,13 @@ int gks_status(gks_handle_t h);
  * their summed device time in milliseconds since the last reset.  Classes:
  * GKS_KC_RECON (per-cell reconstruction), GKS_KC_FACE (per-face
  * reconstruction and gas-kinetic flux), GKS_KC_UPDATE (stage update),
- * GKS_KC_DT (wave-speed reduction and time step). */
+ * GKS_KC_DT (wave-speed reduction and time step), GKS_KC_STAGE (the fused
+ * reconstruction + flux + update kernel of one stage). */
 #define GKS_KC_RECON 0
 #define GKS_KC_FACE 1
 #define GKS_KC_UPDATE 2
 #define GKS_KC_DT 3
+#define GKS_KC_STAGE 4
 /* on != 0 starts (0 stops) the bracketing; reset != 0 zeroes the counts.
  * GKS_ERR_ARG for a NULL handle, GKS_ERR_OOM / GKS_ERR_CUDA if the events
  * cannot be created. */

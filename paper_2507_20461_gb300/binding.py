@@ -47,6 +47,7 @@ class Opts(C.Structure):
         ("mu", C.c_double),
         ("ao_d0", C.c_double),
         ("teno_ct", C.c_double),
+        ("stage_kernels", C.c_int),
     ]
 
 
@@ -251,7 +252,7 @@ def gks_status(h) -> int:
     return _check(h, lib().gks_status(h))
 
 
-KC_RECON, KC_FACE, KC_UPDATE, KC_DT = 0, 1, 2, 3
+KC_RECON, KC_FACE, KC_UPDATE, KC_DT, KC_STAGE = 0, 1, 2, 3, 4
 
 
 def gks_profile_enable(h, on: bool = True, reset: bool = True):
@@ -362,7 +363,7 @@ class Solver:
     """Handle wrapper: ``Solver(n=(nx, ny), lo, hi, gamma, bc, precision)``."""
 
     def __init__(self, n, lo=None, hi=None, gamma=1.4, bc=BC_PERIODIC, precision=0, limiter=0, stream=None, order=None,
-                 **consts):
+                 stage_kernels=0, **consts):
         self.grid = make_grid(n, lo, hi)
         self.dim = len(n)
         self.nv = self.dim + 2
@@ -370,6 +371,7 @@ class Solver:
         o = default_opts()
         o.precision = precision
         o.limiter = limiter
+        o.stage_kernels = stage_kernels
         _set_consts(o, consts)
         sp = _stream_ptr(stream)
         o.stream = sp.value if sp is not None else None

@@ -168,6 +168,11 @@ int two_stages(gks_ctx *c)
         if ((e = gks::nc_launch_step(c)) != cudaSuccess) return cuda_fail(c, e, "RK4 step");
         return GKS_OK;
     }
+    if (c->fused) {
+        if ((e = gks::launch_fused2d(c, 1)) != cudaSuccess) return cuda_fail(c, e, "stage 1");
+        if ((e = gks::launch_fused2d(c, 2)) != cudaSuccess) return cuda_fail(c, e, "stage 2");
+        return GKS_OK;
+    }
     if ((e = run_flux(c, 0, true)) != cudaSuccess) return cuda_fail(c, e, "stage 1 flux");
     if ((e = run_update(c, 1)) != cudaSuccess) return cuda_fail(c, e, "stage 1 update");
     if ((e = run_flux(c, 1, true)) != cudaSuccess) return cuda_fail(c, e, "stage 2 flux");
@@ -242,6 +247,7 @@ int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const
     if (opts) o = *opts;
     if (o.precision != 0 && o.precision != 1) return fail(nullptr, GKS_ERR_ARG, "precision must be 0 or 1");
     if (o.limiter < 0 || o.limiter > 3) return fail(nullptr, GKS_ERR_ARG, "limiter must be 0..3");
+    if (o.stage_kernels != 0 && o.stage_kernels != 1) return fail(nullptr, GKS_ERR_ARG, "stage_kernels must be 0 or 1");
     if (o.limiter >= 2 && (!(o.ao_d0 > 0.0) || !(o.ao_d0 < 1.0) || !(o.teno_ct > 0.0) || !(o.teno_ct < 1.0)))
         return fail(nullptr, GKS_ERR_ARG, "ao_d0 and teno_ct must lie in (0, 1)");
     if (!(o.C > 0.0) || !(o.eps > 0.0) || !(o.C0 > 0.0) || !(o.c1_tau >= 0.0) || !(o.c2_tau >= 0.0) ||
@@ -304,6 +310,7 @@ int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const
     }
     c->B_elems = L.B_elems;
     c->ff_elems = L.ff_elems;
+    c->fused = (L.shadows && grid->dim == 2 && o.stage_kernels == 1) ? 1 : 0;
 
     gks::KP &P = c->kp;
     std::memset(&P, 0, sizeof(P));

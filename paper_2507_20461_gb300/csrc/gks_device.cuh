@@ -62,9 +62,11 @@ template <> struct RT<float> {
     __device__ static float abs_(float x) { return fabsf(x); }
 };
 
-/* Primitive description of a Maxwellian: density, velocity, 1/(2 lambda) = p/rho. */
+/* Primitive description of a Maxwellian: density, velocity, pressure,
+ * 1/(2 lambda) = p/rho, lambda = rho/(2p), and 1/rho (each reciprocal taken
+ * once per Maxwellian and shared by every moment and slope of it). */
 template <typename R, int M> struct Prim {
-    R rho, U[3], p, i2l; /* i2l = 1 / (2 lambda) */
+    R rho, U[3], p, i2l, lam, inv; /* i2l = 1 / (2 lambda), inv = 1 / rho */
 };
 
 template <typename R, int M>
@@ -82,6 +84,8 @@ __device__ __forceinline__ bool to_prim(const R *W, R gm1, Prim<R, M> &P)
     }
     P.p = gm1 * (W[M + 1] - R(0.5) * ke);
     P.i2l = P.p * inv;
+    P.lam = R(0.5) / P.i2l;
+    P.inv = inv;
     return (W[0] > R(0)) && (P.p > R(0));
 }
 
@@ -105,14 +109,14 @@ __device__ __forceinline__ void full_moments(R U, R i2l, R *m)
 
 /* half-space u moments: sign = +1 integrates u > 0, -1 integrates u < 0 */
 template <typename R, int N>
-__device__ __forceinline__ void half_moments(R U, R rho, R p, R i2l, int sign, R *m)
+__device__ __forceinline__ void half_moments(R U, R lam, R i2l, int sign, R *m)
 {
-    const R sl = RT<R>::sqrt_(R(0.5) * rho / p); /* sqrt(lambda) */
-    const R x = sl * U;
+    const R isl = RT<R>::rsqrt_(lam); /* 1 / sqrt(lambda) */
+    const R x = lam * isl * U;        /* sqrt(lambda) U */
     const R s = R(sign);
     m[0] = R(0.5) * RT<R>::erfc_(-s * x);
     /* exp(-lambda U^2) / (2 sqrt(pi lambda)) */
-    m[1] = U * m[0] + s * R(0.5) * RT<R>::exp_(-x * x) * R(0.56418958354775628) / sl;
+    m[1] = U * m[0] + s * R(0.5) * RT<R>::exp_(-x * x) * R(0.56418958354775628) * isl;
 #pragma unroll
     for (int k = 0; k + 2 < N; ++k) m[k + 2] = U * m[k + 1] + R(k + 1) * i2l * m[k];
 }
@@ -316,7 +320,7 @@ __device__ __forceinline__ void slope_moments(const Mom<R, M> &Tm, const R (*s)[
  * closed form through the peculiar velocity c = u - U:
  * <c_i a> = alpha_i / (2 lambda), and the two scalar moments give alpha_1, alpha_E. */
 template <typename R, int M>
-__device__ __forceinline__ void slope(const Prim<R, M> &P, R Ntot, const R *r, R *a)
+__device__ __forceinline__ void slope(const Prim<R, M> &P, R Ntot, R c8N, const R *r, R *a)
 {
     R sv[3], Us = R(0), U2 = R(0);
     const R s0 = r[0];
@@ -327,8 +331,8 @@ __device__ __forceinline__ void slope(const Prim<R, M> &P, R Ntot, const R *r, R
         U2 += P.U[i] * P.U[i];
     }
     const R sE = r[M + 1] - R(0.5) * U2 * s0 - Us;
-    const R lam = R(0.5) / P.i2l;
-    const R aE = R(8) * lam * lam / Ntot * sE - R(2) * lam * s0;
+    const R lam = P.lam;
+    const R aE = c8N * lam * lam * sE - R(2) * lam * s0; /* c8N = 8 / Ntot */
     const R a1 = s0 - aE * Ntot * R(0.5) * P.i2l;
     R aU = R(0);
 #pragma unroll
@@ -356,7 +360,7 @@ __device__ __forceinline__ void euler_flux(const Prim<R, M> &P, const R *W, int 
 template <typename R, int M>
 __device__ __forceinline__ void euler_dflux(const Prim<R, M> &P, const R *W, R gm1, int e, const R *dW, R *dF)
 {
-    const R inv = R(1) / P.rho;
+    const R inv = P.inv;
     R dU[3], UdU = R(0), U2 = R(0);
 #pragma unroll
     for (int i = 0; i < M; ++i) {
@@ -375,9 +379,9 @@ __device__ __forceinline__ void euler_dflux(const Prim<R, M> &P, const R *W, R g
  * FP32 kernel issues no FP64 instruction for them (fill with fill_flux). */
 struct FluxParams {
     double gamma, c1, c2;
-    double gm1, Ntot;      /* gamma - 1, 2 / (gamma - 1) */
+    double gm1, Ntot, c8N; /* gamma - 1, 2 / (gamma - 1), 8 / Ntot */
     double mu;             /* dynamic viscosity (Navier-Stokes flux only) */
-    float fgm1, fNtot, fc1, fc2, fmu;
+    float fgm1, fNtot, fc8N, fc1, fc2, fmu;
 };
 
 /* the constant in the precision R */
@@ -394,8 +398,10 @@ inline void fill_flux(FluxParams &fp, double gamma, double c1, double c2)
     fp.c2 = c2;
     fp.gm1 = gamma - 1.0;
     fp.Ntot = 2.0 / (gamma - 1.0);
+    fp.c8N = 8.0 / fp.Ntot;
     fp.fgm1 = (float)fp.gm1;
     fp.fNtot = (float)fp.Ntot;
+    fp.fc8N = (float)fp.c8N;
     fp.fc1 = (float)c1;
     fp.fc2 = (float)c2;
     fp.fmu = (float)fp.mu;
@@ -413,13 +419,14 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
     constexpr int NV = M + 2;
     const R gm1 = pick<R>(fp.gm1, fp.fgm1);
     const R Ntot = pick<R>(fp.Ntot, fp.fNtot);
+    const R c8N = pick<R>(fp.c8N, fp.fc8N);
     const R K = Ntot - R(M);
     Prim<R, M> Pl, Pr, P0;
     if (!to_prim<R, M>(Wl, gm1, Pl) || !to_prim<R, M>(Wr, gm1, Pr)) return false;
 
     Mom<R, M> Tl, Tr, T0;
-    half_moments<R, 7>(Pl.U[0], Pl.rho, Pl.p, Pl.i2l, +1, Tl.u);
-    half_moments<R, 7>(Pr.U[0], Pr.rho, Pr.p, Pr.i2l, -1, Tr.u);
+    half_moments<R, 7>(Pl.U[0], Pl.lam, Pl.i2l, +1, Tl.u);
+    half_moments<R, 7>(Pr.U[0], Pr.lam, Pr.i2l, -1, Tr.u);
     tangential_and_internal<R, M>(Pl, K, Tl);
     tangential_and_internal<R, M>(Pr, K, Tr);
 
@@ -448,7 +455,7 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
     /* micro-slopes along every face axis */
     R sl[M][NV], sr[M][NV], s0[M][NV], dW0[M][NV];
     {
-        const R il = R(1) / Pl.rho, ir = R(1) / Pr.rho, i0 = R(1) / P0.rho;
+        const R il = Pl.inv, ir = Pr.inv, i0 = P0.inv;
 #pragma unroll
         for (int e = 0; e < M; ++e) {
             R rl[NV], rr[NV], r0[NV];
@@ -459,9 +466,9 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
                 dW0[e][b] = R(0.5) * (dWl[e][b] + dWr[e][b]);
                 r0[b] = dW0[e][b] * i0;
             }
-            slope<R, M>(Pl, Ntot, rl, sl[e]);
-            slope<R, M>(Pr, Ntot, rr, sr[e]);
-            slope<R, M>(P0, Ntot, r0, s0[e]);
+            slope<R, M>(Pl, Ntot, c8N, rl, sl[e]);
+            slope<R, M>(Pr, Ntot, c8N, rr, sr[e]);
+            slope<R, M>(P0, Ntot, c8N, r0, s0[e]);
         }
     }
     /* dW0/dt = -sum_e dF_e/dx_e, dF_n/dt, Euler flux of W0 */
@@ -511,15 +518,15 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
         }
         R Al[NV], Ar[NV];
         {
-            const R il = R(1) / Pl.rho, ir = R(1) / Pr.rho;
+            const R il = Pl.inv, ir = Pr.inv;
 #pragma unroll
             for (int b = 0; b < NV; ++b) {
                 Wlt[b] *= il;
                 Wrt[b] *= ir;
             }
         }
-        slope<R, M>(Pl, Ntot, Wlt, Al);
-        slope<R, M>(Pr, Ntot, Wrt, Ar);
+        slope<R, M>(Pl, Ntot, c8N, Wlt, Al);
+        slope<R, M>(Pr, Ntot, c8N, Wrt, Ar);
         R fl[NV], fr[NV], hl[NV], hr[NV];
 #pragma unroll
         for (int b = 0; b < NV; ++b) fl[b] = fr[b] = hl[b] = hr[b] = R(0);

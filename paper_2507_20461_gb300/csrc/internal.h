@@ -21,6 +21,8 @@ struct gks_ctx {
      * of the stage-1 output (s1) that the reconstruction and flux read */
     gks::Shadow s0, s1;
     int shadows;
+    /* 2D mixed precision with the fused stage kernel (opts.stage_kernels == 1) */
+    int fused;
     /* mixed precision: the steps keep the gradients in s0.g only; G is
      * filled from it when the state is read */
     int g_stale;
@@ -98,6 +100,8 @@ template <int M> cudaError_t launch_shadow(gks_ctx *c);
  * stage input (input 0: W, 1: Ws), and one classical RK4 step */
 cudaError_t nc_launch_faces(gks_ctx *c, int input, double *fs_dev, bool flux);
 cudaError_t nc_launch_step(gks_ctx *c);
+/* 2D mixed precision: one stage (1 or 2) as one fused kernel */
+cudaError_t launch_fused2d(gks_ctx *c, int stage);
 
 inline int ngauss(int m) { return m == 1 ? 1 : (m == 2 ? 2 : 4); }
 inline int ncubic(int m) { return m == 2 ? GENO_NC2 : (m == 3 ? GENO_NC3 : 0); }

@@ -500,6 +500,92 @@ __device__ __forceinline__ bool ext_cell(const KP &P, long t, int &i, int &j, in
     return out <= 1;
 }
 
+/* The blended GENO cubic of one variable of one cell (Sec. 3, Sec. 4.3 on
+ * Cartesian cells): the least-squares cubic from the cross data d (neighbour
+ * differences and cell-unit gradients, Cubic<R, M>::fit order), its
+ * indicators, the 2m linear sub-polynomials and the path function, blended
+ * into one cubic b = chi p^3 + (1 - chi) sum_k w_k p_k (coefficient M-1-a
+ * multiplies xi_a); WENO-Z / TENO in the adaptive-order combination. */
+template <typename R, int M>
+__device__ __forceinline__ void blend_cubic(const KP &P, const R *d, R *b)
+{
+    constexpr int NC = Cubic<R, M>::NC;
+    R c[NC];
+    Cubic<R, M>::fit(d, c);
+    /* blended cubic: chi c, plus lin on the linear monomials */
+    R chi = R(1), lin[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) lin[a] = R(0);
+    if (P.limiter != 1) {
+        R ISH, ISt;
+        Cubic<R, M>::ind(c, ISH, ISt);
+        /* linear sub-polynomials on {cell, neighbour q}: g_e = (s dW + D_e)/2, g_t = D_t */
+        R IS[2 * M], g[2 * M][M];
+#pragma unroll
+        for (int q = 0; q < 2 * M; ++q) {
+            const int e = q / 2;
+            const R s = (q & 1) ? R(1) : R(-1);
+            R sum = R(0);
+#pragma unroll
+            for (int a = 0; a < M; ++a) {
+                const R D = d[q * (1 + M) + 1 + a];
+                g[q][a] = (a == e) ? R(0.5) * (s * d[q * (1 + M)] + D) : D;
+                sum += g[q][a] * g[q][a];
+            }
+            IS[q] = sum;
+        }
+        if (P.limiter == 0) {
+            R smin = IS[0], smax = IS[0], ssum = R(0);
+#pragma unroll
+            for (int q = 0; q < 2 * M; ++q) {
+                smin = fmin(smin, IS[q]);
+                smax = fmax(smax, IS[q]);
+                ssum += IS[q];
+            }
+            const R ISL = (ssum - smin - smax) * R(1.0 / (2 * M - 2));
+            chi = chi_of<R>(P, ISt, ISH, ISL, 3);
+            const R eps = pick<R>(P.eps, P.feps);
+            R ws = R(0);
+#pragma unroll
+            for (int q = 0; q < 2 * M; ++q) {
+                const R wq = R(1) / ((IS[q] + eps) * (IS[q] + eps));
+                ws += wq;
+#pragma unroll
+                for (int a = 0; a < M; ++a) lin[a] += wq * g[q][a];
+            }
+            const R iws = R(1) / ws;
+#pragma unroll
+            for (int a = 0; a < M; ++a) lin[a] = (R(1) - chi) * (lin[a] * iws);
+        } else {
+            /* WENO-Z / TENO, adaptive-order combination: (w0/d0) p^3 +
+             * sum_q (w_q - (w0/d0) d_q) p_q, the 2m linear polynomials
+             * sharing 1 - d0 equally */
+            const R d0 = pick<R>(P.d0, P.fd0), dq = (R(1) - d0) * R(1.0 / (2 * M));
+            R d[2 * M + 1], I[2 * M + 1], w[2 * M + 1];
+            d[0] = d0;
+            I[0] = ISH;
+#pragma unroll
+            for (int q = 0; q < 2 * M; ++q) {
+                d[q + 1] = dq;
+                I[q + 1] = IS[q];
+            }
+            ao_weights<R, 2 * M>(P, d, I, ISt, w);
+            chi = w[0] / d0;
+#pragma unroll
+            for (int q = 0; q < 2 * M; ++q) {
+                const R cq = w[q + 1] - chi * dq;
+#pragma unroll
+                for (int a = 0; a < M; ++a) lin[a] += cq * g[q][a];
+            }
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < NC; ++kk) {
+        b[kk] = chi * c[kk];
+        if (kk < M) b[kk] += lin[M - 1 - kk];
+    }
+}
+
 template <typename R, int M>
 __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R *__restrict__ B, long t)
 {
@@ -560,83 +646,11 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R
                 d[2 * M * (1 + M) + a] = (((sm[0] >> v) ^ (sm[0] >> (8 + a))) & 1u) ? -g : g;
             }
         }
-        R c[NC];
-        Cubic<R, M>::fit(d, c);
-        /* blended cubic: chi c, plus lin on the linear monomials */
-        R chi = R(1), lin[M];
-#pragma unroll
-        for (int a = 0; a < M; ++a) lin[a] = R(0);
-        if (P.limiter != 1) {
-            R ISH, ISt;
-            Cubic<R, M>::ind(c, ISH, ISt);
-            /* linear sub-polynomials on {cell, neighbour q}: g_e = (s dW + D_e)/2, g_t = D_t */
-            R IS[2 * M], g[2 * M][M];
-#pragma unroll
-            for (int q = 0; q < 2 * M; ++q) {
-                const int e = q / 2;
-                const R s = (q & 1) ? R(1) : R(-1);
-                R sum = R(0);
-#pragma unroll
-                for (int a = 0; a < M; ++a) {
-                    const R D = d[q * (1 + M) + 1 + a];
-                    g[q][a] = (a == e) ? R(0.5) * (s * d[q * (1 + M)] + D) : D;
-                    sum += g[q][a] * g[q][a];
-                }
-                IS[q] = sum;
-            }
-            if (P.limiter == 0) {
-                R smin = IS[0], smax = IS[0], ssum = R(0);
-#pragma unroll
-                for (int q = 0; q < 2 * M; ++q) {
-                    smin = fmin(smin, IS[q]);
-                    smax = fmax(smax, IS[q]);
-                    ssum += IS[q];
-                }
-                const R ISL = (ssum - smin - smax) * R(1.0 / (2 * M - 2));
-                chi = chi_of<R>(P, ISt, ISH, ISL, 3);
-                const R eps = pick<R>(P.eps, P.feps);
-                R ws = R(0);
-#pragma unroll
-                for (int q = 0; q < 2 * M; ++q) {
-                    const R wq = R(1) / ((IS[q] + eps) * (IS[q] + eps));
-                    ws += wq;
-#pragma unroll
-                    for (int a = 0; a < M; ++a) lin[a] += wq * g[q][a];
-                }
-                const R iws = R(1) / ws;
-#pragma unroll
-                for (int a = 0; a < M; ++a) lin[a] = (R(1) - chi) * (lin[a] * iws);
-            } else {
-                /* WENO-Z / TENO, adaptive-order combination: (w0/d0) p^3 +
-                 * sum_q (w_q - (w0/d0) d_q) p_q, the 2m linear polynomials
-                 * sharing 1 - d0 equally */
-                const R d0 = pick<R>(P.d0, P.fd0), dq = (R(1) - d0) * R(1.0 / (2 * M));
-                R d[2 * M + 1], I[2 * M + 1], w[2 * M + 1];
-                d[0] = d0;
-                I[0] = ISH;
-#pragma unroll
-                for (int q = 0; q < 2 * M; ++q) {
-                    d[q + 1] = dq;
-                    I[q + 1] = IS[q];
-                }
-                ao_weights<R, 2 * M>(P, d, I, ISt, w);
-                chi = w[0] / d0;
-#pragma unroll
-                for (int q = 0; q < 2 * M; ++q) {
-                    const R cq = w[q + 1] - chi * dq;
-#pragma unroll
-                    for (int a = 0; a < M; ++a) lin[a] += cq * g[q][a];
-                }
-            }
-        }
-        /* (coefficient M-1-a multiplies xi_a) */
+        R b[NC];
+        blend_cubic<R, M>(P, d, b);
         const long base = (long)v * NC;
 #pragma unroll
-        for (int kk = 0; kk < NC; ++kk) {
-            R b = chi * c[kk];
-            if (kk < M) b += lin[M - 1 - kk];
-            B[(base + kk) * P.next + t] = b;
-        }
+        for (int kk = 0; kk < NC; ++kk) B[(base + kk) * P.next + t] = b[kk];
     }
 }
 
@@ -1019,6 +1033,86 @@ __device__ __forceinline__ long face_of(const KP &P, int d, int i, int j, int k,
     return P.foff[d] + ((long)idx[2] * e1 + idx[1]) * e0 + idx[0];
 }
 
+/* The mixed-precision stage update of one cell from the FP32 face sums over
+ * the Gauss points, fsum(q, v, d, plus): q = 0 F, 1 dF/dt, 2 W(dt/2) of
+ * variable v on the cell's face of direction d (plus = 1 the upper face).
+ * A cell adds its faces' fluxes exactly (double-float accumulation), so each
+ * face's flux leaves one cell and enters the other without a rounding of its
+ * own, and the stage combination runs in double-float FP32 arithmetic (about
+ * 48 bits; GB300's FP64 rate is 1/64 of FP32).  Stage 1 writes the next
+ * input directly as its FP32 shadow s1 (= s0 + increment) and keeps Acc as a
+ * float pair acc[2][nv][cell]; stage 2 adds its increment to the FP64 state W
+ * and re-splits W into s0, so the shadow never drifts from W.  The sums of
+ * the averages are conserved to FP64 rounding.  Gradients (not conserved)
+ * come from FP32 differences of the interface states and live in the shadow
+ * only (Eq. slope).  mixed_update_var updates variable v and returns its new
+ * FP32 value; mixed_update_cell all variables and the admissibility flags. */
+template <int M, int STAGE, typename FaceSum>
+__device__ __forceinline__ float mixed_update_var(const KP &P, const FaceSum &fsum, const UpdC &uc,
+                                                 double *__restrict__ W, float *__restrict__ acc, const Shadow &s0,
+                                                 const Shadow &s1, long cell, int v)
+{
+    constexpr int NV = M + 2, NG = (M == 2) ? 2 : 4;
+    const long nc = P.ncell;
+    const float gw = P.fih / NG;
+    const Shadow &so = (STAGE == 1) ? s1 : s0;
+    float sF = 0.f, eF = 0.f, sT = 0.f, eT = 0.f;
+#pragma unroll
+    for (int d = 0; d < M; ++d) {
+        if (STAGE == 1) {
+            two_sum_acc(sF, eF, fsum(0, v, d, 1));
+            two_sum_acc(sF, eF, -fsum(0, v, d, 0));
+        }
+        two_sum_acc(sT, eT, fsum(1, v, d, 1));
+        two_sum_acc(sT, eT, -fsum(1, v, d, 0));
+        so.g[(d * NV + v) * nc + cell] = (fsum(2, v, d, 1) - fsum(2, v, d, 0)) * gw;
+    }
+    const F2 ST{sT, eT};
+    if (STAGE == 1) {
+        const F2 SF{sF, eF};
+        const F2 dW = df_add(df_mul(uc.k[0], SF), df_mul(uc.k[1], ST));
+        const F2 A = df_add(df_mul(uc.k[2], SF), df_mul(uc.k[3], ST));
+        acc[v * nc + cell] = A.hi;
+        acc[(NV + v) * nc + cell] = A.lo;
+        const F2 w = df_add(F2{s0.hi[v * nc + cell], s0.lo[v * nc + cell]}, dW);
+        so.hi[v * nc + cell] = w.hi;
+        so.lo[v * nc + cell] = w.lo;
+        return w.hi;
+    } else {
+        const F2 dW = df_add(F2{acc[v * nc + cell], acc[(NV + v) * nc + cell]}, df_mul(uc.k[4], ST));
+        const double w = (W[v * nc + cell] + (double)dW.hi) + (double)dW.lo;
+        W[v * nc + cell] = w;
+        split_store(w, so.hi, so.lo, v * nc + cell);
+        return (float)w;
+    }
+}
+
+/* admissibility flags of a new state from the FP32 values of its variables */
+template <int M> __device__ __forceinline__ void mixed_state_flags(const KP &P, const float *wn, int *__restrict__ status)
+{
+    float ke = 0.f;
+#pragma unroll
+    for (int a = 0; a < M; ++a) ke += wn[1 + a] * wn[1 + a];
+    const float p = P.fgm1 * (wn[M + 1] - 0.5f * ke / wn[0]);
+    int st = 0;
+    if (!(wn[0] > 0.f)) st |= ST_RHO;
+    if (!(p > 0.f)) st |= ST_P;
+    if (!isfinite(p) || !isfinite(wn[0])) st |= ST_NAN;
+    if (st) atomicOr(status, st);
+}
+
+template <int M, int STAGE, typename FaceSum>
+__device__ __forceinline__ void mixed_update_cell(const KP &P, const FaceSum &fsum, const UpdC &uc,
+                                                  double *__restrict__ W, float *__restrict__ acc, const Shadow &s0,
+                                                  const Shadow &s1, int *__restrict__ status, long cell)
+{
+    constexpr int NV = M + 2;
+    float wn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) wn[v] = mixed_update_var<M, STAGE>(P, fsum, uc, W, acc, s0, s1, cell, v);
+    mixed_state_flags<M>(P, wn, status);
+}
+
 /* STAGE 1: Ws = W - dt/2 L(F) - dt^2/8 L(Ft), Gs = Gauss(W(dt/2)), Acc = -dt L(F) - dt^2/6 L(Ft)
  * STAGE 2: W += Acc - dt^2/3 L(Ft*),        G  = Gauss(W*(dt/2))
  * with L(q)_j = (1/h) sum_d sum_g w_g (q(+d face) - q(-d face)). */
@@ -1031,76 +1125,23 @@ __device__ __forceinline__ void update_item(const KP &P, const R *__restrict__ f
     constexpr int NV = M + 2, NG = (M == 1) ? 1 : ((M == 2) ? 2 : 4);
     if constexpr (sizeof(R) == sizeof(float) && M >= 2) {
         /* mixed precision: the face values are per-face FP32 sums over the
-         * Gauss points (ff[q][v][face]).  A cell adds its faces' fluxes
-         * exactly (double-float accumulation), so each face's flux leaves one
-         * cell and enters the other without a rounding of its own, and the
-         * stage combination runs in double-float FP32 arithmetic (about 48
-         * bits; GB300's FP64 rate is 1/64 of FP32).  Stage 1 writes the next
-         * input directly as its FP32 shadow s1 (= s0 + increment) and keeps
-         * Acc as a float pair; stage 2 adds its increment to the FP64 state
-         * W and re-splits W into s0, so the shadow never drifts from W.  The
-         * sums of the averages are conserved to FP64 rounding.  Gradients
-         * (not conserved) come from FP32 differences and live in the shadow
-         * only; the FP64 G is filled from it when the state is read. */
+         * Gauss points (ff[q][v][face]); see mixed_update_cell */
         unsigned q0, q1;
         const int i = (int)fdivmod(P.dn[0], (unsigned)cell, q0);
         const int j = (int)fdivmod(P.dn[1], q0, q1);
         const int k = (M >= 3) ? (int)q1 : 0;
-        const long nft = P.nftot, nc = P.ncell;
-        const float gw = P.fih / NG;
+        const long nft = P.nftot;
         long fp[M], fm[M];
 #pragma unroll
         for (int d = 0; d < M; ++d) {
             fp[d] = face_of<M>(P, d, i, j, k, 1);
             fm[d] = face_of<M>(P, d, i, j, k, 0);
         }
-        float *acc = (float *)Acc; /* [2][nv][cell]: hi, lo */
-        const Shadow &so = (STAGE == 1) ? s1 : s0;
-        float wn[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const float *f0 = ff + (long)(0 * NV + v) * nft, *f1 = ff + (long)(1 * NV + v) * nft,
-                        *f2 = ff + (long)(2 * NV + v) * nft;
-            float sF = 0.f, eF = 0.f, sT = 0.f, eT = 0.f;
-#pragma unroll
-            for (int d = 0; d < M; ++d) {
-                if (STAGE == 1) {
-                    two_sum_acc(sF, eF, f0[fp[d]]);
-                    two_sum_acc(sF, eF, -f0[fm[d]]);
-                }
-                two_sum_acc(sT, eT, f1[fp[d]]);
-                two_sum_acc(sT, eT, -f1[fm[d]]);
-                so.g[(d * NV + v) * nc + cell] = (f2[fp[d]] - f2[fm[d]]) * gw;
-            }
-            const F2 ST{sT, eT};
-            if (STAGE == 1) {
-                const F2 SF{sF, eF};
-                const F2 dW = df_add(df_mul(uc.k[0], SF), df_mul(uc.k[1], ST));
-                const F2 A = df_add(df_mul(uc.k[2], SF), df_mul(uc.k[3], ST));
-                acc[v * nc + cell] = A.hi;
-                acc[(NV + v) * nc + cell] = A.lo;
-                const F2 w = df_add(F2{s0.hi[v * nc + cell], s0.lo[v * nc + cell]}, dW);
-                so.hi[v * nc + cell] = w.hi;
-                so.lo[v * nc + cell] = w.lo;
-                wn[v] = w.hi;
-            } else {
-                const F2 dW = df_add(F2{acc[v * nc + cell], acc[(NV + v) * nc + cell]}, df_mul(uc.k[4], ST));
-                const double w = (W[v * nc + cell] + (double)dW.hi) + (double)dW.lo;
-                W[v * nc + cell] = w;
-                split_store(w, so.hi, so.lo, v * nc + cell);
-                wn[v] = (float)w;
-            }
-        }
-        /* admissibility flags from the FP32 values of the new state */
-        float ke = 0.f;
-#pragma unroll
-        for (int a = 0; a < M; ++a) ke += wn[1 + a] * wn[1 + a];
-        const float p = P.fgm1 * (wn[M + 1] - 0.5f * ke / wn[0]);
-        int st = 0;
-        if (!(wn[0] > 0.f)) st |= ST_RHO;
-        if (!(p > 0.f)) st |= ST_P;
-        if (!isfinite(p) || !isfinite(wn[0])) st |= ST_NAN;
-        if (st) atomicOr(status, st);
+        /* face sums ff[q][v][face] of the cell's faces */
+        auto fsum = [&](int q, int v, int d, int plus) -> float {
+            return ff[(long)(q * NV + v) * nft + (plus ? fp[d] : fm[d])];
+        };
+        mixed_update_cell<M, STAGE>(P, fsum, uc, W, (float *)Acc, s0, s1, status, cell);
         return;
     }
     unsigned q0, q1 = 0;

@@ -86,10 +86,10 @@ def test_static_flux_walls_and_weight_variants(bc, limiter):
     W, G, h = _state(nx, ny, 11 + limiter + 3 * bc)
     ref = _reference(nx, ny, h, bc, W, G, dt, limiter)
     o = _opts(limiter)
+    Wd, Gd = torch.from_numpy(W).to(DEV), torch.from_numpy(G).to(DEV)  # kept alive across the call
     for _ in range(2):
         out = torch.full((ref.size,), float("nan"), dtype=torch.float64, device=DEV)
-        r = f(nx, ny, h, 1.4, bc, C.byref(o), torch.from_numpy(W).to(DEV).data_ptr(),
-              torch.from_numpy(G).to(DEV).data_ptr(), dt, out.data_ptr(), stream)
+        r = f(nx, ny, h, 1.4, bc, C.byref(o), Wd.data_ptr(), Gd.data_ptr(), dt, out.data_ptr(), stream)
         assert r == B.OK
         got = out.cpu().numpy()
         np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
@@ -108,11 +108,11 @@ def test_static_flux_reports_a_nonphysical_state():
     ke = 0.5 * (Wbad[1] ** 2 + Wbad[2] ** 2) / Wbad[0]
     Wbad[3, 6:9, 8:11] = ke[6:9, 8:11] - 1.0
     out = torch.zeros(3 * 4 * 2 * ((nx + 1) * ny + nx * (ny + 1)), dtype=torch.float64, device=DEV)
-    r = f(nx, ny, h, 1.4, B.BC_PERIODIC, None, torch.from_numpy(Wbad).to(DEV).data_ptr(),
-          torch.from_numpy(G).to(DEV).data_ptr(), dt, out.data_ptr(), stream)
+    Wb, Gd = torch.from_numpy(Wbad).to(DEV), torch.from_numpy(G).to(DEV)  # kept alive across the calls
+    r = f(nx, ny, h, 1.4, B.BC_PERIODIC, None, Wb.data_ptr(), Gd.data_ptr(), dt, out.data_ptr(), stream)
     assert r == B.ERR_NONPHYSICAL
     ref = _reference(nx, ny, h, B.BC_PERIODIC, W, G, dt)
-    r = f(nx, ny, h, 1.4, B.BC_PERIODIC, None, torch.from_numpy(W).to(DEV).data_ptr(),
-          torch.from_numpy(G).to(DEV).data_ptr(), dt, out.data_ptr(), stream)
+    Wd = torch.from_numpy(W).to(DEV)
+    r = f(nx, ny, h, 1.4, B.BC_PERIODIC, None, Wd.data_ptr(), Gd.data_ptr(), dt, out.data_ptr(), stream)
     assert r == B.OK
     np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
