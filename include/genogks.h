@@ -230,6 +230,20 @@ int gks_profile_enable(gks_handle_t h, int on, int reset);
  * NULL handle or a class outside 0..7. */
 int gks_profile_read(gks_handle_t h, int kernel_class, long *launches, double *ms);
 
+/* Measured throughput of one arithmetic pipe of the current device, the
+ * denominator of the stage kernels' rooflines (the paper has no
+ * counterpart: measurement infrastructure).  kind 0: FP32 fused multiply-add
+ * (2 flops each), 1: FP64 fused multiply-add, 2: the FP32 special-function
+ * unit (ex2.approx, 1 op each).  A grid of 8 blocks of 256 threads per SM
+ * runs iters x 32 operations per thread on eight independent chains; the
+ * second of two launches is timed with CUDA events on `stream` (NULL = the
+ * legacy default stream), which the call synchronises.  *ops_per_s receives
+ * flops (or ops) per second.  Allocates a small scratch buffer with
+ * cudaMallocAsync on `stream` and frees it before returning.
+ * GKS_ERR_ARG for a bad kind, iters < 1 or NULL output; GKS_ERR_OOM /
+ * GKS_ERR_CUDA if the allocation or a launch fails. */
+int gks_pipe_probe(int kind, int iters, double *ops_per_s, void *stream);
+
 /* Free everything the handle owns (not a caller workspace).  NULL is a no-op. */
 int gks_destroy(gks_handle_t h);
 

@@ -1348,8 +1348,8 @@ int or_step(const or_cfg *c, double dt, double *W, double *G)
     double *Ws = (double *)malloc(sizeof(double) * nv * nc);
     double *Gs = (double *)malloc(sizeof(double) * m * nv * nc);
     int r = OR_ERR_ARG;
-    if (!f1 || !f2 || !Ws || !Gs) goto done;
     double h = c->h;
+    if (!f1 || !f2 || !Ws || !Gs) goto done;
     /* stage 1 from (W^n, G^n) */
     r = or_flux(c, dt, W, G, f1);
     if (r) goto done;

@@ -13,7 +13,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgenogks.so")
-SOURCES = ["k1d.cu", "k2d.cu", "k3d.cu", "k2d_batch.cu", "k2d_fused.cu", "api.cu", "batch.cu", "static_flux.cu", "analysis.cu", "k1d_nc.cu"]
+SOURCES = ["k1d.cu", "k2d.cu", "k3d.cu", "k2d_batch.cu", "k2d_fused.cu", "api.cu", "batch.cu", "static_flux.cu", "analysis.cu", "probe.cu", "k1d_nc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -104,6 +104,7 @@ def lib(build: bool = True):
         "gks_batch_last_error": (C.c_char_p, [vp]),
         "gks_batch_tuning": (C.c_char_p, [vp]),
         "geno_linearity": (C.c_int, [op, C.c_int, C.c_int, C.c_int, C.c_long, vp, vp, vp, vp]),
+        "gks_pipe_probe": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double), vp]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -433,3 +434,15 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+PIPE_FFMA, PIPE_DFMA, PIPE_MUFU = 0, 1, 2
+
+
+def pipe_probe(kind: int, iters: int, stream=None) -> float:
+    """Measured throughput (flops or ops per second) of one arithmetic pipe:
+    PIPE_FFMA, PIPE_DFMA (2 flops per FMA) or PIPE_MUFU (1 op per ex2)."""
+    out = C.c_double()
+    sp = _stream_ptr(stream)
+    _check(None, lib().gks_pipe_probe(int(kind), int(iters), C.byref(out), sp))
+    return float(out.value)
