@@ -12,6 +12,10 @@ precision device-timed rate; `fp64` holds the FP64 path's; `e2e` is the same
 metric through the C ABI with host buffers (state copied in from pinned host
 memory and read back every step).  `--impl reference` times the oracle (the
 plain CPU implementation) on the host cores instead.
+
+Rooflines: algorithmic flops per unit from the oracle's operation count
+(tests/golden/flop_counts.json) against the pipe throughput the library's
+probe kernels measure on this GPU (FP32 FMA, FP64 FMA).
 Multi-GPU: replicas only (independent grids per rank, no exchange).
 """
 from __future__ import annotations
@@ -35,23 +39,70 @@ CFL = 0.4
 METRIC = "cell-updates/s and % HBM roofline, 2D 2048² mixed vs FP64, at stated L1 err"
 WORKLOAD = "2D Euler 2048x2048 periodic, 16 random-phase density modes (k<=8) + 4 planar shocks Mach U[1.5,3], CFL 0.4"
 
-# Algorithmic work per unit of the dominant kernel (face_flux_kernel), counted
-# by ncu (2 x FMA + ADD + MUL instructions of the pipe) on a 256^2 case in
-# which every face Gauss point is evaluated exactly once:
-#   mixed path: 1764 FP32 flops per face Gauss point;
-#   FP64 path:  2021 FP64 flops per face Gauss point (mean of the stages).
-# (the face-flux flop summary under profiles/)
-FLOPS_PER_FACE_GP = {"mixed": 1764.0, "fp64": 2021.0}
-# DRAM bytes (read + write) per launch of the face-flux kernel, from one
-# 1-pass ncu capture each (mixed at 1024^2: 168.1 MB read + 40.9 MB written;
-# FP64 at 256^2: 21.27 MB read; the face-flux summaries under profiles/),
-# scaled to the 2048^2 launch by the Gauss points it processes (the traffic is the coefficient array read
-# about once plus the face sums written, both proportional to the grid).
-TRAFFIC_PER_FLUX_LAUNCH = {"mixed": 209.06e6 * (2049 * 2048) / (1025 * 1024),
-                           "fp64": 21.266e6 * (2049 * 2048) / (257 * 256)}
+# Algorithmic work per unit, from the oracle's operation count
+# (tests/golden/flop_counts.json, written by tests/golden/make_flop_counts.py:
+# the oracle's own arithmetic with common subexpressions shared and constants
+# folded; flops = add/sub + mul + div, an FMA is 2; exp, erfc, sqrt and tanh
+# are one op each and counted apart).
+FLOPS = json.load(open(os.path.join(ROOT, "tests", "golden", "flop_counts.json")))
+
+
+def _flops(key):
+    return FLOPS[key]["flops"]
+
+
+def _trans(key):
+    return FLOPS[key]["transcendental"]
+
+
+# face_flux_kernel, per face Gauss point: both interface states from the
+# cubics (evaluation, admissibility) and the gas-kinetic flux
+FACE_GP_2D = _flops("gks_point_2d") + _flops("face_states_gp_2d")
+FACE_GP_2D_TRANS = _trans("gks_point_2d") + _trans("face_states_gp_2d")
+# one cell advanced one full two-stage step (every kernel of the step)
+CELL_UPDATE_2D = _flops("step_cell_update_2d")
+CELL_UPDATE_3D = _flops("step_cell_update_3d")
+# Navier-Stokes in 3D: the Euler step plus, per stage, the 12 face Gauss
+# points of a cell with the viscous flux's extra work
+CELL_UPDATE_3D_NS = CELL_UPDATE_3D + 2 * 12 * (_flops("gks_point_3d_ns") - _flops("gks_point_3d"))
+# the WENO-Z / TENO weights change only the cubic of each (cell, variable)
+CELL_UPDATE_2D_LIMITER = {lim: CELL_UPDATE_2D + 2 * 4 * (_flops(f"cubic_cell_var_2d_limiter{lim}")
+                                                         - _flops("cubic_cell_var_2d_limiter0")) for lim in (2, 3)}
+# 1D non-compact GENO + HLLC, one classical RK4 step (4 stages)
+NC_CELL_UPDATE = {o: _flops(f"nc_step_cell_update_1d_order{o}") for o in (5, 6)}
+# Executed flops of the face-flux kernel itself (ncu: 2 x FMA + ADD + MUL of
+# the pipe, per face Gauss point, on a 256^2 case where every point is
+# evaluated once; the face-flux flop summary under profiles/).  The kernel
+# uses closed forms where the oracle solves moment systems, so it executes
+# fewer flops than the algorithmic count.
+EXECUTED_FLOPS_PER_FACE_GP = {"mixed": None, "fp64": None}
+# DRAM bytes (read + write) per launch of the face-flux kernel from a 1-pass
+# ncu capture (None until captured for the current kernel).
+TRAFFIC_PER_FLUX_LAUNCH = {"mixed": None, "fp64": None}
 # Algorithmic HBM bytes per cell-update of the whole step (FP64 state,
 # stage buffers, accumulator), 2D: 60 doubles.
 BYTES_PER_CELL_UPDATE = 480.0
+
+
+def measured_pipes(B):
+    """Measured throughput of the arithmetic pipes (the library's probe
+    kernels, CUDA-event timed): FP32 FMA and FP64 FMA in TFLOP/s, the
+    special-function unit in Tops/s."""
+    return {"ffma_tflops": B.pipe_probe(B.PIPE_FFMA, 4096) / 1e12,
+            "dfma_tflops": B.pipe_probe(B.PIPE_DFMA, 64) / 1e12,
+            "mufu_tops": B.pipe_probe(B.PIPE_MUFU, 256) / 1e12}
+
+
+def alu_roofline(flops_per_unit, units_per_s, peak, kernel, unit_of_work, peak_source, traffic=None, nominal=None):
+    """Roofline entry of a compute-bound kernel: algorithmic flops per unit x
+    units per second against a measured pipe peak (TFLOP/s)."""
+    ach = flops_per_unit * units_per_s / 1e12
+    r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+         "kernel": kernel, "flops_per_unit": flops_per_unit, "unit_of_work": unit_of_work,
+         "numerator": "oracle op count (tests/golden/flop_counts.json)", "peak_source": peak_source}
+    if nominal:
+        r["frac_of_nominal"] = ach / nominal
+    return r
 
 
 def _peaks():
@@ -210,10 +261,11 @@ def run_reference(args):
     return 0
 
 
-def time_path(B, torch, W, G, h, precision, steps, warmup, dev, limiter=0):
+def time_path(B, torch, W, G, h, precision, steps, warmup, dev, limiter=0, stage_kernels=0):
     """Device-timed steps of one precision; returns (ms/step, profile, final density)."""
     stream = torch.cuda.current_stream()
-    s = B.Solver((N, N), bc=B.BC_PERIODIC, precision=precision, stream=stream, limiter=limiter)
+    s = B.Solver((N, N), bc=B.BC_PERIODIC, precision=precision, stream=stream, limiter=limiter,
+                 stage_kernels=stage_kernels)
     Wd = torch.from_numpy(W).to(dev)
     Gd = torch.from_numpy(G).to(dev)
     s.set_state(Wd, Gd)
@@ -227,7 +279,7 @@ def time_path(B, torch, W, G, h, precision, steps, warmup, dev, limiter=0):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    prof = {k: s.profile_read(k) for k in (B.KC_RECON, B.KC_FACE, B.KC_UPDATE, B.KC_DT)}
+    prof = {k: s.profile_read(k) for k in (B.KC_RECON, B.KC_FACE, B.KC_UPDATE, B.KC_DT, B.KC_STAGE)}
     s.profile(False, False)
     st = s.status()
     s.get_state(Wd, Gd)
@@ -236,7 +288,7 @@ def time_path(B, torch, W, G, h, precision, steps, warmup, dev, limiter=0):
     return ms, prof, rho, st
 
 
-def time_limiters(B, torch, W, G, h, steps, warmup, dev, ms_geno):
+def time_limiters(B, torch, W, G, h, steps, warmup, dev, ms_geno, ffma):
     """The WENO-Z and TENO weight variants (limiter 2, 3) on the headline
     workload, mixed precision, through the same timed path: they change only
     the per-cell reconstruction, so the face flux (the roofline kernel) is the
@@ -249,11 +301,13 @@ def time_limiters(B, torch, W, G, h, steps, warmup, dev, ms_geno):
             "vs_geno_ms": ms / ms_geno,
             "kernel_ms": {nm: prof[k][1] / max(prof[k][0], 1) for k, nm in
                           ((B.KC_RECON, "cell_poly"), (B.KC_FACE, "face_flux"), (B.KC_UPDATE, "update"))},
+            "roofline": alu_roofline(CELL_UPDATE_2D_LIMITER[lim], N * N / (ms * 1e-3), ffma, "whole step (all kernels)",
+                                     "cell-update", "measured: FFMA probe"),
         }
     return out
 
 
-def time_noncompact(B, torch, steps, dev):
+def time_noncompact(B, torch, steps, dev, dfma):
     """The 1D non-compact GENO schemes (order 5 and 6, HLLC flux, classical
     RK4; FP64) on 2^22 cells of the config-1 family (seeded two-state Riemann
     problem, transmissive), through gks_step_cfl.  Throughput and the split
@@ -289,6 +343,8 @@ def time_noncompact(B, torch, steps, dev):
         out[f"order{order}"] = {
             "value": n / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps, "status": st,
             "kernel_ms_per_step": {"faces": prof[B.KC_FACE][1] / steps, "rk4_update": prof[B.KC_UPDATE][1] / steps},
+            "roofline": alu_roofline(NC_CELL_UPDATE[order], n / (ms * 1e-3), dfma, "whole RK4 step (FP64)",
+                                     "cell-update", "measured: DFMA probe"),
         }
     return out
 
@@ -340,56 +396,84 @@ def aggregate(ws, ms_local, dist=None, device=None):
     return t.tolist()
 
 
-def time_batch(B, torch, steps, dev):
+def time_batch(B, torch, dev, ffma, total_steps=300, warm=3):
     """Config 4: 256 independent grids, sides log-uniform in [64, 1024], four-
-    quadrant ICs (seed 20464 + i), transmissive, CFL 0.4; mixed precision timed
-    with the graph replay; density L1 of mixed against the FP64 batch after 3
-    equal steps."""
+    quadrant ICs (seed inputs.batch_seed(i): 20464 + i, the recorded grids
+    redrawn), transmissive, CFL 0.4, the configuration's full 300 steps:
+    `warm` steps (tuning, graph recording) and the remaining steps timed,
+    mixed precision, graph replay.  The FP64 batch of the sampled grids runs
+    the same 300 steps (each grid its own CFL time step, so the grids are
+    independent of the rest), once from the input and once from the input
+    perturbed at FP32 rounding size; density L1 / L-inf of mixed against FP64
+    per sampled grid at step 300 (the worst grid is reported), with the
+    perturbed FP64 run's beside it."""
+    import numpy as np
+
     from paper_2507_20461_gb300 import inputs as I
 
     sides = I.batch_sizes(256, seed=20464)
     hs = [1.0 / n for n in sides]
     cells = sum(n * n for n in sides)
-    states = [I.quadrants_2d(n, seed=20464 + g)[:2] for g, n in enumerate(sides)]
+    states = [I.quadrants_2d(n, seed=I.batch_seed(g))[:2] for g, n in enumerate(sides)]
     out = {}
     rho = {}
     sample = (0, 1, 2, 100, 255)
-    for prec in (1, 0):
-        # mixed: all 256 grids (timed); FP64 reference: the sampled grids only
-        # (grids are independent, so their results do not depend on the rest)
+    steps = total_steps - warm
+    rng = np.random.default_rng(7)
+    # runs: mixed (all grids, timed), FP64 and FP64 from the input perturbed
+    # by a seeded relative 2^-24 (the sampled grids: the workload's own
+    # sensitivity to rounding-size differences, beside mixed vs FP64)
+    for run in ("mixed", "fp64", "fp64_perturbed"):
+        prec = 1 if run == "mixed" else 0
         ids = list(range(len(sides))) if prec == 1 else list(sample)
         bt = B.Batch([sides[g] for g in ids], [sides[g] for g in ids], [hs[g] for g in ids],
                      bc=B.BC_TRANSMISSIVE, precision=prec)
         for k, g in enumerate(ids):
             W, G = states[g]
-            bt.set_state(k, torch.from_numpy(W).to(dev), torch.from_numpy(G).to(dev))
-        bt.run(CFL, 3)  # tuning + graph recording + 3 steps
+            if run == "fp64_perturbed":
+                W = W * (1.0 + 2.0**-24 * rng.uniform(-1.0, 1.0, size=W.shape))
+            bt.set_state(k, torch.from_numpy(np.ascontiguousarray(W)).to(dev), torch.from_numpy(G).to(dev))
+        bt.run(CFL, warm)  # tuning + graph recording + warm steps
         torch.cuda.synchronize()
-        rho[prec] = []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        bt.run(CFL, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        rho[run] = []
         for g in sample:
             Wd = torch.from_numpy(states[g][0]).to(dev)
             Gd = torch.from_numpy(states[g][1]).to(dev)
             bt.get_state(ids.index(g), Wd, Gd)
-            rho[prec].append(Wd[0].clone())
-        if prec == 1:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            stream = torch.cuda.current_stream()
-            e0.record(stream)
-            bt.run(CFL, steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / steps
+            rho[run].append(Wd[0].clone())
+        if run == "mixed":
             out = {"value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps,
-                   "grids": 256, "cells": cells, "status": bt.status(), "tuning": json.loads(bt.tuning() or "{}")}
+                   "total_steps": total_steps, "grids": 256, "cells": cells, "status": bt.status(),
+                   "tuning": json.loads(bt.tuning() or "{}"),
+                   "roofline": alu_roofline(CELL_UPDATE_2D, cells / (ms * 1e-3), ffma, "whole batched step",
+                                            "cell-update", "measured: FFMA probe")}
+        elif run == "fp64":
+            out["fp64_sampled_ms_per_step"] = ms
+            out["fp64_status"] = bt.status()
         bt.close()
-    l1 = max(float((a - b).abs().mean()) for a, b in zip(rho[1], rho[0]))
-    out["l1_density_mixed_vs_fp64_3_steps"] = l1
-    out["workload"] = "256 grids, sides log-uniform [64,1024], four-quadrant ICs, transmissive, mixed precision, graph replay"
+    spread = [(float((a - b).abs().mean()), float((a - b).abs().max()))
+              for a, b in zip(rho["fp64_perturbed"], rho["fp64"])]
+    errs = [(float((a - b).abs().mean()), float((a - b).abs().max())) for a, b in zip(rho["mixed"], rho["fp64"])]
+    out[f"l1_density_mixed_vs_fp64_{total_steps}_steps"] = max(e[0] for e in errs)
+    out[f"linf_density_mixed_vs_fp64_{total_steps}_steps"] = max(e[1] for e in errs)
+    out[f"l1_density_fp64_perturbed_{total_steps}_steps"] = max(e[0] for e in spread)
+    out["sampled_grids"] = {str(g): {"side": sides[g], "l1": e[0], "linf": e[1], "l1_fp64_perturbed": p[0],
+                                     "linf_fp64_perturbed": p[1]} for g, e, p in zip(sample, errs, spread)}
+    out["workload"] = ("256 grids, sides log-uniform [64,1024], four-quadrant ICs, transmissive, mixed precision, "
+                       "graph replay, 300 steps")
+    out["redrawn_grids"] = {str(g): I.batch_seed(g) for g in I.BATCH_REDRAWS}
     return out
 
 
-def time_3d(B, torch, steps, dev):
+def time_3d(B, torch, steps, dev, ffma):
     """Config 5: 3D 256^3 periodic solenoidal turbulence (rms Mach 0.6), mixed precision."""
     from paper_2507_20461_gb300 import inputs as I
 
@@ -412,6 +496,8 @@ def time_3d(B, torch, steps, dev):
     st = s.status()
     s.close()
     return {"value": n**3 / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps, "status": st,
+            "roofline": alu_roofline(CELL_UPDATE_3D, n**3 / (ms * 1e-3), ffma, "whole step (all kernels)",
+                                     "cell-update", "measured: FFMA probe"),
             "workload": "3D 256^3 periodic solenoidal velocity (E(k) ~ k^4 exp(-2(k/4)^2), rms Mach 0.6), mixed precision"}
 
 
@@ -437,7 +523,7 @@ def run_case(n, precision, steps):
     return 0 if st == 0 else 1
 
 
-def time_tgv(B, torch, steps, dev):
+def time_tgv(B, torch, steps, dev, ffma):
     """Navier-Stokes: the Taylor-Green vortex (u0 = 1, Ma 0.1, Re = 1600 with
     L0 = 2 pi, Prandtl 1) on 256^3 periodic cells of [-pi, pi]^3, mixed
     precision, through gks_step_cfl with the viscous time-step limit.  Its
@@ -466,6 +552,8 @@ def time_tgv(B, torch, steps, dev):
     st = s.status()
     s.close()
     return {"value": n**3 / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps, "status": st,
+            "roofline": alu_roofline(CELL_UPDATE_3D_NS, n**3 / (ms * 1e-3), ffma, "whole step (all kernels)",
+                                     "cell-update", "measured: FFMA probe"),
             "workload": "3D Taylor-Green vortex 256^3, Navier-Stokes (Re 1600, Ma 0.1, Pr 1), mixed precision"}
 
 
@@ -519,10 +607,12 @@ def main():
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    pipes = measured_pipes(B)
     ms_mixed, prof_mixed, rho_mixed, st_mixed = time_path(B, torch, W, G, h, 1, args.steps, args.warmup, dev)
+    ms_fused, prof_fused, _, st_fused = time_path(B, torch, W, G, h, 1, args.steps, args.warmup, dev, stage_kernels=1)
     ms_fp64, prof_fp64, rho_fp64, st_fp64 = time_path(B, torch, W, G, h, 0, steps64, args.warmup, dev)
     torch.cuda.synchronize()
-    ms_mixed, ms_fp64 = aggregate(ws, [ms_mixed, ms_fp64], dist if ws > 1 else None, dev)
+    ms_mixed, ms_fused, ms_fp64 = aggregate(ws, [ms_mixed, ms_fused, ms_fp64], dist if ws > 1 else None, dev)
     clk = clocks.stop()
 
     # mixed vs FP64 on the same CFL steps (the FP64 path's time steps drive
@@ -550,40 +640,62 @@ def main():
             for key, (_, Wd_, _) in zip(errors, runs[1:]):
                 drho = (Wd_[0] - runs[0][1][0]).abs()
                 errors[key][str(step)] = {"l1": float(drho.mean()), "linf": float(drho.max())}
-    l1 = errors["mixed_vs_fp64"][str(L1_STEPS)]["l1"]
-    linf = errors["mixed_vs_fp64"][str(L1_STEPS)]["linf"]
     st_l1 = [s_.status() for s_, _, _ in runs]
     for s_, _, _ in runs:
         s_.close()
     del runs, Wp
+    accuracy = {}
+    for k in err_at:
+        accuracy[f"l1_density_mixed_vs_fp64_{k}"] = errors["mixed_vs_fp64"][str(k)]["l1"]
+        accuracy[f"linf_density_mixed_vs_fp64_{k}"] = errors["mixed_vs_fp64"][str(k)]["linf"]
+        accuracy[f"l1_density_fp64_perturbed_{k}"] = errors["fp64_input_2^-24_vs_fp64"][str(k)]["l1"]
+        accuracy[f"linf_density_fp64_perturbed_{k}"] = errors["fp64_input_2^-24_vs_fp64"][str(k)]["linf"]
 
     e2e_val, h2d, d2h = time_e2e(B, torch, W, G, 1, max(2, min(args.steps, 5)), 1, dev)
-    batch = time_batch(B, torch, max(3, min(args.steps, 20)), dev) if not args.headline_only else None
-    three_d = time_3d(B, torch, max(3, min(args.steps, 10)), dev) if not args.headline_only else None
-    tgv = time_tgv(B, torch, max(3, min(args.steps, 10)), dev) if not args.headline_only else None
+    ffma, dfma = pipes["ffma_tflops"], pipes["dfma_tflops"]
+    batch = None if args.headline_only else _guarded(time_batch, B, torch, dev, ffma)
+    three_d = None if args.headline_only else _guarded(time_3d, B, torch, max(3, min(args.steps, 10)), dev, ffma)
+    tgv = None if args.headline_only else _guarded(time_tgv, B, torch, max(3, min(args.steps, 10)), dev, ffma)
     limiters = None if args.headline_only else _guarded(
-        time_limiters, B, torch, W, G, h, max(3, min(args.steps, 10)), args.warmup, dev, ms_mixed)
-    noncompact = None if args.headline_only else _guarded(time_noncompact, B, torch, max(3, min(args.steps, 10)), dev)
+        time_limiters, B, torch, W, G, h, max(3, min(args.steps, 10)), args.warmup, dev, ms_mixed, ffma)
+    noncompact = None if args.headline_only else _guarded(
+        time_noncompact, B, torch, max(3, min(args.steps, 10)), dev, dfma)
 
     peaks, peak_src = _peaks()
     sm_clock = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
-    # FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop
+    # nominal unit-count peaks, for context: 152 SMs x 128 FP32 lanes x 2 flop,
+    # and 2 DFMA per SM per clock
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = nsm * 128 * 2 * sm_clock * 1e6 / 1e12
-    # FP64 ALU peak: 2 DFMA per SM per clock (measured by a DFMA probe: 1.25 TFLOP/s at 2070 MHz)
-    fp64_peak = nsm * 2 * 2 * sm_clock * 1e6 / 1e12
+    fp32_nominal = nsm * 128 * 2 * sm_clock * 1e6 / 1e12
+    fp64_nominal = nsm * 2 * 2 * sm_clock * 1e6 / 1e12
 
-    def face_gps():
-        return 2 * (N + 1) * N * 2  # faces of both directions x 2 Gauss points
-
-    n_face, t_face = prof_mixed[B.KC_FACE]
-    # one face-flux launch per direction: units per launch = faces of one direction x 2 Gauss points
-    avg_face_ms = t_face / max(n_face, 1)
+    # the dominant kernel: the face flux, one launch per direction; units per
+    # launch = faces of one direction x 2 Gauss points
     units_per_launch = (N + 1) * N * 2
-    achieved = FLOPS_PER_FACE_GP["mixed"] * units_per_launch / (avg_face_ms * 1e-3) / 1e12
+    n_face, t_face = prof_mixed[B.KC_FACE]
+    avg_face_ms = t_face / max(n_face, 1)
     n64, t64 = prof_fp64[B.KC_FACE]
     avg64 = t64 / max(n64, 1)
-    achieved64 = FLOPS_PER_FACE_GP["fp64"] * units_per_launch / (avg64 * 1e-3) / 1e12
+    roof = alu_roofline(FACE_GP_2D, units_per_launch / (avg_face_ms * 1e-3), ffma, "face_flux_kernel<float,2,D,true>",
+                        "face Gauss point", "measured: FFMA probe", TRAFFIC_PER_FLUX_LAUNCH["mixed"], fp32_nominal)
+    roof["transcendentals_per_unit"] = FACE_GP_2D_TRANS
+    roof["launch_ms"] = avg_face_ms
+    roof["units_per_launch"] = units_per_launch
+    roof64 = alu_roofline(FACE_GP_2D, units_per_launch / (avg64 * 1e-3), dfma, "face_flux_kernel<double,2,D,true>",
+                          "face Gauss point", "measured: DFMA probe", TRAFFIC_PER_FLUX_LAUNCH["fp64"], fp64_nominal)
+    roof64["launch_ms"] = avg64
+    for r, key in ((roof, "mixed"), (roof64, "fp64")):
+        ex = EXECUTED_FLOPS_PER_FACE_GP[key]
+        if ex:
+            r["executed_flops_per_unit"] = ex
+            r["frac_executed"] = r["frac"] * ex / FACE_GP_2D
+    # the fused stage kernel: units per launch = cells (one stage of each)
+    n_st, t_st = prof_fused[B.KC_STAGE]
+    avg_stage_ms = t_st / max(n_st, 1)
+    fused = {"value": ws * N * N / (ms_fused * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms_fused,
+             "stage_launch_ms": avg_stage_ms, "status": st_fused, "vs_three_kernel_ms": ms_fused / ms_mixed,
+             "roofline": alu_roofline(CELL_UPDATE_2D / 2, N * N / (avg_stage_ms * 1e-3), ffma,
+                                      "fused2d_stage_kernel", "cell-stage", "measured: FFMA probe")}
 
     launches_per_step = 1 + 1 + 2 * (1 + 2 + 1)  # wavespeed, dt, 2 x (poly, 2 face dirs, update)
     value = ws * N * N / (ms_mixed * 1e-3)
@@ -616,20 +728,19 @@ def main():
             "l2": "inputs larger than L2 (state 403 MB per copy)",
             "parallelism": f"replicas x{ws}",
         },
-        "fp64": {"value": value64, "ms_per_step": ms_fp64, "steps": steps64,
-                 "roofline": {"bound": "alu", "achieved": achieved64, "peak": fp64_peak, "unit": "TFLOP/s",
-                              "frac": achieved64 / fp64_peak, "traffic": TRAFFIC_PER_FLUX_LAUNCH["fp64"]}},
-        "l1_density_mixed_vs_fp64": l1,
-        "linf_density_mixed_vs_fp64": linf,
-        "error_steps": L1_STEPS,
+        "fp64": {"value": value64, "ms_per_step": ms_fp64, "steps": steps64, "roofline": roof64,
+                 "whole_step_roofline": alu_roofline(CELL_UPDATE_2D, value64 / ws, dfma, "whole step (all kernels)",
+                                                     "cell-update", "measured: DFMA probe")},
+        **accuracy,
         "density_errors": errors,
         "hbm_roofline_frac": hbm_frac,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": TRAFFIC_PER_FLUX_LAUNCH["mixed"],
-                     "kernel": "face_flux_kernel<float,2,D,true>",
-                     "peak_source": "FP32: SMs x 128 lanes x 2 flop x max SM clock"},
+        "roofline": roof,
+        "whole_step_roofline": alu_roofline(CELL_UPDATE_2D, value / ws, ffma, "whole step (all kernels)",
+                                            "cell-update", "measured: FFMA probe"),
+        "measured_pipes": pipes,
         "kernel_ms": {name: prof_mixed[k][1] / max(prof_mixed[k][0], 1) for k, name in
                       ((B.KC_RECON, "cell_poly"), (B.KC_FACE, "face_flux"), (B.KC_UPDATE, "update"), (B.KC_DT, "dt"))},
+        "fused_stage_kernel": fused,
         "status": {"mixed": st_mixed, "fp64": st_fp64, "error_run": st_l1},
         "e2e": {"value": ws * e2e_val, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,

@@ -330,18 +330,27 @@ int gks_batch_set_state(gks_batch_t b, int grid, const double *W, const double *
 int gks_batch_get_state(gks_batch_t b, int grid, double *W, double *G, int on_device);
 
 /* nsteps steps of every grid, grid b with dt_b = cfl h_b / (its max |u_d| + c)
- * computed on the device.  Per stage three persistent kernels (per-cell
- * reconstruction, face flux of both directions, update) walk a tile work list
- * spanning all grids.  The first call times tile-size / block-size candidates
- * for each kernel (an autotuner; only scratch buffers are written), then
- * records one step into a CUDA graph; later calls replay the graph (a new cfl
- * re-records it).  Asynchronous with respect to the host; ordered after the
- * work already on opts->stream, and later work on that stream waits for it. */
+ * computed on the device.  Mixed precision: per stage one launch of the
+ * fused stage kernel (reconstruction, flux and update through shared
+ * memory), one block per strip of a list spanning every grid; FP64: per
+ * stage three
+ * persistent kernels (per-cell reconstruction, face flux, update) walk tile
+ * lists spanning all grids.  The first call picks the tile sizes (rows per
+ * strip) and block sizes by timing candidates (an autotuner; only scratch
+ * buffers are written), then records one step into a CUDA graph; later calls
+ * replay the graph (a new cfl re-records it).  The tuner's choices are cached
+ * per (dimension, precision, limiter, size class of the batch, SM count): in
+ * the process, and in the file named by the environment variable
+ * GKS_TUNE_CACHE if set (one JSON object per line, appended); a batch whose
+ * size class is cached skips the timing.  Asynchronous with respect to the
+ * host; ordered after the work already on opts->stream, and later work on
+ * that stream waits for it. */
 int gks_batch_run(gks_batch_t b, double cfl, int nsteps);
 
 /* JSON text of the launch shapes the tuner picked (per kernel class: block
- * size, items per tile, persistent blocks, measured ms); "" before the first
- * gks_batch_run.  Owned by the handle. */
+ * size, items per tile or rows per strip, persistent blocks, measured ms;
+ * "cached": true and no timings when they came from the cache, with the
+ * size-class key); "" before the first gks_batch_run.  Owned by the handle. */
 const char *gks_batch_tuning(gks_batch_t b);
 
 /* Synchronise and return the status word (as gks_status). */

@@ -94,3 +94,9 @@ def genomd_cells(dim: int, cells, limiter=0) -> list[dict]:
     for c in cells:
         buf += _f64(c)
     return _run(["cell", dim, len(cells), limiter], bytes(buf))
+
+
+def nc_step(order: int, n: int, h: float, dt: float, W, gamma=1.4, bc=0) -> dict:
+    """Counts of one classical RK4 step of the 1D non-compact GENO scheme of
+    the given order (5 or 6) with the HLLC flux on n cells (or_nc_step)."""
+    return _run(["ncstep", order, n, repr(h), repr(dt), gamma, bc], _f64(W))[0]

@@ -8,6 +8,7 @@
  *   opcount gks  m ncases gamma c1 c2 tau_mode mu     per case Wl, Wr, dWl, dWr, dt
  *   opcount step|flux|recon dim n0 n1 n2 h dt gamma bc limiter    W, G of the grid
  *   opcount cell dim ncells limiter                   per cell the or_genomd_cell input
+ *   opcount ncstep order n h dt gamma bc              W of a 1D grid (non-compact GENO, HLLC, RK4)
  * Data values enter as inputs (fresh nodes); the scheme constants, h and dt
  * as constants.
  */
@@ -152,6 +153,20 @@ int main(int argc, char **argv)
         std::snprintf(extra, sizeof extra, ", \"faces\": %ld, \"gauss_points\": %ld, \"status\": %d", nft,
                       nft * ng, r);
         print_counts(mode.c_str(), cells, extra);
+        return 0;
+    }
+    if (mode == "ncstep") {
+        const int order = std::atoi(argv[2]);
+        const int n[3] = {std::atoi(argv[3]), 1, 1};
+        const double h = std::atof(argv[4]), dt = std::atof(argv[5]), gamma = std::atof(argv[6]);
+        const int bc = std::atoi(argv[7]);
+        const or_cfg c = make_cfg(1, n, h, gamma, bc, 0);
+        std::vector<ocn> W = inputs(read_doubles((size_t)3 * n[0]));
+        opc::reset();
+        const int r = or_nc_step(&c, order, dt, W.data());
+        char extra[64];
+        std::snprintf(extra, sizeof extra, ", \"status\": %d", r);
+        print_counts("ncstep", n[0], extra);
         return 0;
     }
     if (mode == "cell") {

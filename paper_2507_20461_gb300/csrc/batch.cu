@@ -1,13 +1,25 @@
 /* C ABI of the batched 2D mode (gks_batch_*): many independent grids of
  * uneven sizes, persistent kernels over tile work lists, per-grid time steps
- * on the device, one step captured into a CUDA graph and replayed.  The
- * tile size and block size of every kernel class are picked by timing the
- * candidates on the actual grids before the graph is recorded. */
+ * on the device, one step captured into a CUDA graph and replayed.  Mixed
+ * precision runs each stage as one persistent launch of the fused stage
+ * kernel over a list of strips of every grid (one block per strip); FP64
+ * runs the three kernel
+ * classes (reconstruction, flux, update).  The tile size and block size of
+ * every kernel class are picked by timing the candidates on the actual grids
+ * before the graph is recorded; the choices are cached per (dimension,
+ * precision, size class of the batch, SM count), in the process and, if the
+ * environment variable GKS_TUNE_CACHE names a file, in that file (one JSON
+ * object per line), so a batch of the same size class skips the timing. */
 #include <cmath>
 #include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "batch.h"
@@ -43,7 +55,7 @@ struct gks_batch_ctx {
     cudaGraphExec_t exec;
     double graph_cfl;
     int nsm;
-    char tuning[512];
+    char tuning[768];
     char err[256];
 };
 
@@ -115,6 +127,17 @@ long items(const gks::KP &P, int k, int dir)
     }
 }
 
+/* the strips of the fused stage kernel: per grid, columns in strips of
+ * kStageStrip, rows in chunks of `rows` */
+void stage_tiles(const gks_batch_ctx *b, long rows, std::vector<Tile> &v)
+{
+    for (int g = 0; g < b->nb; ++g) {
+        const gks::KP &P = b->hd[g].P;
+        for (int x0 = 0; x0 < P.n[0]; x0 += gks::kStageStrip)
+            for (long y0 = 0; y0 < P.n[1]; y0 += rows) v.push_back(Tile{g, x0, y0, y0 + rows < P.n[1] ? y0 + rows : P.n[1]});
+    }
+}
+
 int build_tiles(gks_batch_ctx *b, int k, long tile)
 {
     /* the previous list may still be read by work on the internal stream */
@@ -124,7 +147,8 @@ int build_tiles(gks_batch_ctx *b, int k, long tile)
      * of the FP32 face mapping, whose face sums synchronise the block) */
     if (k == gks::BK_FLUX && tile % 128 != 0) return bfail(b, GKS_ERR_ARG, "flux tiles must be whole 128-item groups");
     std::vector<Tile> v;
-    for (int g = 0; g < b->nb; ++g) {
+    if (k == gks::BK_STAGE) stage_tiles(b, tile, v);
+    for (int g = 0; g < b->nb && k != gks::BK_STAGE; ++g) {
         const gks::KP &P = b->hd[g].P;
         const int ndir = (k == gks::BK_FLUX) ? 2 : 1;
         for (int d = 0; d < ndir; ++d) {
@@ -144,7 +168,7 @@ int build_tiles(gks_batch_ctx *b, int k, long tile)
 
 BatchLaunch launch_of(gks_batch_ctx *b, int k)
 {
-    return BatchLaunch{b->dd, b->tiles[k], b->ntiles[k], b->dt, b->smax, b->status};
+    return BatchLaunch{b->dd, b->tiles[k], b->ntiles[k], b->dt, b->smax, b->status, &b->hd[0].P};
 }
 
 cudaError_t run_class(gks_batch_ctx *b, int k, int stage)
@@ -154,9 +178,11 @@ cudaError_t run_class(gks_batch_ctx *b, int k, int stage)
     const bool f = b->precision == 1;
     switch (k) {
     case gks::BK_SPEED: return f ? gks::batch_speed<float>(L, S, b->stream) : gks::batch_speed<double>(L, S, b->stream);
-    case gks::BK_POLY: return f ? gks::batch_poly<float>(L, S, stage, b->stream) : gks::batch_poly<double>(L, S, stage, b->stream);
-    case gks::BK_FLUX: return f ? gks::batch_flux<float>(L, S, stage, b->stream) : gks::batch_flux<double>(L, S, stage, b->stream);
-    default: return f ? gks::batch_update<float>(L, S, stage, b->stream) : gks::batch_update<double>(L, S, stage, b->stream);
+    /* the three stage kernels run the FP64 batches; mixed precision runs the fused stage kernel */
+    case gks::BK_POLY: return f ? cudaErrorInvalidValue : gks::batch_poly<double>(L, S, stage, b->stream);
+    case gks::BK_FLUX: return f ? cudaErrorInvalidValue : gks::batch_flux<double>(L, S, stage, b->stream);
+    case gks::BK_STAGE: return f ? gks::batch_stage(L, S, stage, b->stream) : cudaErrorInvalidValue;
+    default: return f ? cudaErrorInvalidValue : gks::batch_update<double>(L, S, stage, b->stream);
     }
 }
 
@@ -167,6 +193,10 @@ int enqueue_step(gks_batch_ctx *b, double cfl)
     if (e == cudaSuccess) e = run_class(b, gks::BK_SPEED, 1);
     if (e == cudaSuccess) e = gks::batch_dt(b->dd, b->nb, cfl, b->smax, b->dt, b->stream);
     for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage) {
+        if (b->precision == 1) {
+            e = run_class(b, gks::BK_STAGE, stage);
+            continue;
+        }
         e = run_class(b, gks::BK_POLY, stage);
         if (e == cudaSuccess) e = run_class(b, gks::BK_FLUX, stage);
         if (e == cudaSuccess) e = run_class(b, gks::BK_UPDATE, stage);
@@ -192,27 +222,148 @@ float time_class(gks_batch_ctx *b, int k)
     return ms;
 }
 
-/* Autotuner: for every kernel class, tile size x block size candidates,
- * persistent grid = SMs x resident blocks; keep the fastest.  Runs only
- * kernels that write scratch (wave speeds, coefficients, face fluxes, stage-1
- * outputs), so the state is unchanged. */
+/* The kernel classes a batch runs: mixed precision the wave speed and the
+ * fused stage kernel, FP64 the wave speed and the three stage kernels. */
+std::vector<int> classes_of(const gks_batch_ctx *b)
+{
+    if (b->precision == 1) return {gks::BK_SPEED, gks::BK_STAGE};
+    return {gks::BK_SPEED, gks::BK_POLY, gks::BK_FLUX, gks::BK_UPDATE};
+}
+
+const char *class_name(int k)
+{
+    static const char *names[] = {"speed", "poly", "flux", "update", "stage"};
+    return names[k];
+}
+
+/* Size class of a batch: powers of two of the grid count, of the total cell
+ * count and of the largest side, with the dimension, precision, limiter
+ * and the device's SM count. */
+std::string size_class(const gks_batch_ctx *b)
+{
+    long cells = 0;
+    int side = 0;
+    for (int g = 0; g < b->nb; ++g) {
+        cells += b->hd[g].P.ncell;
+        side = std::max(side, std::max(b->hd[g].P.n[0], b->hd[g].P.n[1]));
+    }
+    auto lg = [](double x) { return (int)std::lround(std::log2(x > 1.0 ? x : 1.0)); };
+    char k[160];
+    snprintf(k, sizeof k, "2d/p%d/l%d/nb%d/cells%d/side%d/sm%d", b->precision, b->opts.limiter, lg(b->nb), lg((double)cells),
+             lg(side), b->nsm);
+    return k;
+}
+
+struct TuneEntry {
+    LaunchShape shape[gks::BK_COUNT];
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune_cache;
+bool g_tune_file_read = false;
+
+/* the cache file named by GKS_TUNE_CACHE: one object per line,
+ * {"key": "...", "shapes": [[block, tile, blocks], ... per kernel class]} */
+void tune_file_read()
+{
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char *path = std::getenv("GKS_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[1024];
+    while (std::fgets(line, sizeof line, f)) {
+        const char *kp = std::strstr(line, "\"key\": \"");
+        const char *sp = std::strstr(line, "\"shapes\": [");
+        if (!kp || !sp) continue;
+        kp += 8;
+        const char *ke = std::strchr(kp, '"');
+        if (!ke) continue;
+        TuneEntry t;
+        const char *q = sp + 11;
+        bool ok = true;
+        for (int k = 0; k < gks::BK_COUNT && ok; ++k) {
+            long v[3];
+            for (int j = 0; j < 3 && ok; ++j) {
+                while (*q && (*q < '0' || *q > '9') && *q != '-') ++q;
+                char *end = nullptr;
+                v[j] = std::strtol(q, &end, 10);
+                ok = end != q;
+                q = end;
+            }
+            if (ok) t.shape[k] = LaunchShape{(int)v[0], v[1], (int)v[2]};
+        }
+        if (ok) g_tune_cache[std::string(kp, ke)] = t;
+    }
+    std::fclose(f);
+}
+
+void tune_file_append(const std::string &key, const TuneEntry &t)
+{
+    const char *path = std::getenv("GKS_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"shapes\": [", key.c_str());
+    for (int k = 0; k < gks::BK_COUNT; ++k)
+        std::fprintf(f, "%s[%d, %ld, %d]", k ? ", " : "", t.shape[k].block, t.shape[k].tile, t.shape[k].blocks);
+    std::fprintf(f, "]}\n");
+    std::fclose(f);
+}
+
+/* the shapes of a cached entry: rebuild the tile lists */
+int apply_shapes(gks_batch_ctx *b, const TuneEntry &t)
+{
+    for (int k : classes_of(b)) {
+        int r = build_tiles(b, k, t.shape[k].tile);
+        if (r) return r;
+        b->shape[k] = t.shape[k];
+    }
+    return GKS_OK;
+}
+
+/* Autotuner: for every kernel class the batch runs, tile size x block size
+ * candidates (the fused stage kernel: rows per strip), persistent grid = SMs
+ * x resident blocks; keep the fastest.  Runs only kernels that write scratch
+ * (wave speeds, coefficients, face fluxes, stage-1 outputs), so the state is
+ * unchanged.  A batch of a size class tuned before (in this process or in
+ * the GKS_TUNE_CACHE file) takes the cached shapes without timing. */
 int tune(gks_batch_ctx *b, double cfl)
 {
+    const std::string key = size_class(b);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_file_read();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            int r = apply_shapes(b, it->second);
+            if (r) return r;
+            int pos = snprintf(b->tuning, sizeof(b->tuning), "{\"cached\": true, \"key\": \"%s\"", key.c_str());
+            for (int k : classes_of(b))
+                pos += snprintf(b->tuning + pos, sizeof(b->tuning) - pos, ", \"%s\": {\"block\": %d, \"tile\": %ld, \"blocks\": %d}",
+                                class_name(k), b->shape[k].block, b->shape[k].tile, b->shape[k].blocks);
+            snprintf(b->tuning + pos, sizeof(b->tuning) - pos, "}");
+            b->tuned = 1;
+            return GKS_OK;
+        }
+    }
     const long tiles[] = {512, 2048, 8192, 32768};
+    const long rows_c[] = {16, 32, 64, 128};
     int pos = 0;
-    pos += snprintf(b->tuning + pos, sizeof(b->tuning) - pos, "{");
-    const int order[] = {gks::BK_SPEED, gks::BK_POLY, gks::BK_FLUX, gks::BK_UPDATE};
-    const char *names[] = {"speed", "poly", "flux", "update"};
-    for (int oi = 0; oi < 4; ++oi) {
-        const int k = order[oi];
+    pos += snprintf(b->tuning + pos, sizeof(b->tuning) - pos, "{\"cached\": false, \"key\": \"%s\"", key.c_str());
+    for (int k : classes_of(b)) {
         const int blocks_c[2] = {128, 256};
-        const int nblk = (k == gks::BK_POLY || k == gks::BK_FLUX) ? 1 : 2;
+        int nblk = (k == gks::BK_POLY || k == gks::BK_FLUX) ? 1 : 2;
+        const bool stg = k == gks::BK_STAGE;
+        if (stg) nblk = 1;
         float best = 1e30f;
-        LaunchShape bs{128, 2048, b->nsm};
+        LaunchShape bs{stg ? 256 : 128, 2048, b->nsm};
         for (int bi = 0; bi < nblk; ++bi) {
-            const int block = blocks_c[bi];
+            const int block = stg ? 256 : blocks_c[bi];
             const int occ = gks::batch_occupancy(k, b->precision, block);
-            for (long t : tiles) {
+            for (int ci = 0; ci < 4; ++ci) {
+                const long t = stg ? rows_c[ci] : tiles[ci];
                 int r = build_tiles(b, k, t);
                 if (r) return r;
                 b->shape[k].block = block;
@@ -235,8 +386,8 @@ int tune(gks_batch_ctx *b, double cfl)
             gks::batch_dt(b->dd, b->nb, cfl, b->smax, b->dt, b->stream);
         }
         if (k == gks::BK_POLY) run_class(b, gks::BK_POLY, 1);
-        pos += snprintf(b->tuning + pos, sizeof(b->tuning) - pos, "%s\"%s\": {\"block\": %d, \"tile\": %ld, \"blocks\": %d, \"ms\": %.4f}",
-                        oi ? ", " : "", names[oi], bs.block, bs.tile, bs.blocks, best);
+        pos += snprintf(b->tuning + pos, sizeof(b->tuning) - pos, ", \"%s\": {\"block\": %d, \"tile\": %ld, \"blocks\": %d, \"ms\": %.4f}",
+                        class_name(k), bs.block, bs.tile, bs.blocks, best);
     }
     snprintf(b->tuning + pos, sizeof(b->tuning) - pos, "}");
     cudaError_t e = cudaStreamSynchronize(b->stream);
@@ -244,6 +395,12 @@ int tune(gks_batch_ctx *b, double cfl)
     /* tuning ran stage-1 kernels only; clear the status they may have set */
     cudaMemset(b->status, 0, sizeof(int));
     b->tuned = 1;
+    TuneEntry t;
+    for (int k = 0; k < gks::BK_COUNT; ++k) t.shape[k] = b->shape[k];
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (g_tune_cache.emplace(key, t).second) tune_file_append(key, t);
+    }
     return GKS_OK;
 }
 
@@ -351,10 +508,11 @@ int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs,
         gks_batch_destroy(b);
         return r;
     }
-    for (int k = 0; k < gks::BK_COUNT; ++k) {
-        const int occ = gks::batch_occupancy(k, b->precision, 128);
-        b->shape[k] = LaunchShape{128, 4096, b->nsm * (occ > 0 ? occ : 1)};
-        int r = build_tiles(b, k, 4096);
+    for (int k : classes_of(b)) {
+        const int block = (k == gks::BK_STAGE) ? 256 : 128;
+        const int occ = gks::batch_occupancy(k, b->precision, block);
+        b->shape[k] = LaunchShape{block, k == gks::BK_STAGE ? 32 : 4096, b->nsm * (occ > 0 ? occ : 1)};
+        int r = build_tiles(b, k, b->shape[k].tile);
         if (r) {
             std::memcpy(g_batch_err, b->err, sizeof(g_batch_err));
             gks_batch_destroy(b);

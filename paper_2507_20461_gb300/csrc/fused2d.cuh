@@ -70,31 +70,46 @@ __device__ __forceinline__ const float *sweep_plane(const Shadow &s, long nc, in
     return (f < 4) ? s.hi + (long)f * nc : (f < 8) ? s.lo + (long)(f - 4) * nc : s.g + (long)(f - 8) * nc;
 }
 
-template <int STAGE, bool NS, int TX, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) fused2d_stage_kernel(KP P, Shadow s0, Shadow s1, double *__restrict__ W,
-                                                                 float *__restrict__ acc,
-                                                                 const double *__restrict__ dtp,
-                                                                 int *__restrict__ status, int rows)
+/* Geometry of one grid: the fields of its parameter block that differ
+ * between the grids of a batch (which share every scheme constant). */
+struct FusedGeo {
+    int nx, ny;
+    long nc;
+    double ih;
+    float fh, fih;
+};
+
+__host__ __device__ __forceinline__ FusedGeo fused_geo(const KP &P)
+{
+    return FusedGeo{P.n[0], P.n[1], P.ncell, P.ih, P.fh, P.fih};
+}
+
+/* The stage on the strip of columns x0 .. x0 + TX - 1, rows y0 .. y0 + rows
+ * - 1 (clipped to the grid), by the NT threads of the calling block; P holds
+ * the scheme constants and boundary types, geo the grid's geometry; smem
+ * holds SweepStrip<TX>::FLOATS floats, uc is block-shared.  Every thread of
+ * the block calls it. */
+template <int STAGE, bool NS, int TX, int NT>
+__device__ __forceinline__ void fused2d_strip(const KP &P, const FusedGeo &geo, const Shadow &s0, const Shadow &s1,
+                                              double *__restrict__ W, float *__restrict__ acc, double dt,
+                                              int *__restrict__ status, int x0, int y0, int rows, float *smem,
+                                              UpdC &uc)
 {
     using T = SweepStrip<TX>;
     constexpr int NV = T::NV, NC = T::NC, WX = T::WX, CX = T::CX;
     static_assert(NT >= 4 * TX && NT % 32 == 0, "the update of a row takes one thread per (cell, variable)");
-    extern __shared__ __align__(16) float smem[];
     float *const S = smem + T::O_STATE; /* [slot][field][WX] */
     float *const Bc = smem + T::O_B;    /* [slot][cx][v * NC + k] */
     float *const W0 = smem + T::O_W0;   /* [slot][cx][v] signed cell averages (FP32 hi) */
     float *const XF = smem + T::O_XF;   /* [ix][g][12] */
     float *const YF = smem + T::O_YF;   /* [slot][ix][g][12] */
-    __shared__ UpdC uc;
 
     const Shadow &sin = (STAGE == 1) ? s0 : s1;
-    const int nx = P.n[0], ny = P.n[1];
-    const long nc = P.ncell;
-    const int x0 = blockIdx.x * TX;
-    const int y0 = blockIdx.y * rows;
+    const int nx = geo.nx, ny = geo.ny;
+    const long nc = geo.nc;
     const int y1 = min(y0 + rows, ny);
     const int tid = threadIdx.x;
-    if (tid == 0) uc = make_updc(dtp[0], P.ih / 2);
+    if (tid == 0) uc = make_updc(dt, geo.ih / 2);
     const bool xin = x0 >= 2 && x0 + TX + 2 <= nx; /* every column of the strip's rows is inside */
 
     /* stage-input row r into its ring slot; cells that need no sign change
@@ -134,7 +149,7 @@ __global__ void __launch_bounds__(NT, MINB) fused2d_stage_kernel(KP P, Shadow s0
         const int v = it / CX, cx = it - v * CX;
         const float *rm = S + ((r - 1) & 3) * T::SROW, *r0 = S + (r & 3) * T::SROW, *rp = S + ((r + 1) & 3) * T::SROW;
         const int wx = cx + 1;
-        const float hr = P.fh;
+        const float hr = geo.fh;
         const int fh = v, fl = 4 + v, fgx = 8 + v, fgy = 12 + v;
         const float h0 = r0[fh * WX + wx], l0 = r0[fl * WX + wx];
         float d[GENO_ND2];
@@ -160,7 +175,7 @@ __global__ void __launch_bounds__(NT, MINB) fused2d_stage_kernel(KP P, Shadow s0
     /* flux work item wi (warp-uniform).  y_only: the y faces between rows
      * j - 1 and j; else the x faces of row j (the first NXB face blocks) and
      * the y faces between rows j and j + 1 */
-    const float dtf = (float)dtp[0];
+    const float dtf = (float)dt;
     auto flux_item = [&](int j, int wi, bool y_only) {
         const int lane = tid & 31, g = wi & 1, fb = wi >> 1;
         const bool xd = !y_only && fb < T::NXB;
@@ -183,7 +198,7 @@ __global__ void __launch_bounds__(NT, MINB) fused2d_stage_kernel(KP P, Shadow s0
         }
         const bool wall = xd ? ((fi == 0 && P.bcs[0][0] >= 2) || (fi == nx && P.bcs[0][1] >= 2))
                              : ((yr == 0 && P.bcs[1][0] >= 2) || (yr == ny && P.bcs[1][1] >= 2));
-        const float gm1 = P.fgm1, ih = P.fih, adm = P.fadm;
+        const float gm1 = P.fgm1, ih = geo.fih, adm = P.fadm;
         float st[2][NV][3], cw[2][NV];
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
@@ -280,7 +295,7 @@ __global__ void __launch_bounds__(NT, MINB) fused2d_stage_kernel(KP P, Shadow s0
                 const float *p = d == 0 ? XF + (tx + plus) * 2 * T::FV : (plus ? yhi : ylo) + tx * 2 * T::FV;
                 return p[q * NV + vv] + p[T::FV + q * NV + vv];
             };
-            wn = mixed_update_var<2, STAGE>(P, fsum, uc, W, acc, s0, s1, (long)j * nx + gx, v);
+            wn = mixed_update_var<2, STAGE>(nc, geo.fih, fsum, uc, W, acc, s0, s1, (long)j * nx + gx, v);
         }
         const int base = (tid & 31) & ~3;
         float w4[NV];
@@ -314,6 +329,19 @@ __global__ void __launch_bounds__(NT, MINB) fused2d_stage_kernel(KP P, Shadow s0
         __syncthreads();
     }
     if (y1 > y0) update_row(y1 - 1);
+}
+
+/* one grid: block (bx, by) sweeps strip bx over the rows' chunk by */
+template <int STAGE, bool NS, int TX, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) fused2d_stage_kernel(KP P, Shadow s0, Shadow s1, double *__restrict__ W,
+                                                                 float *__restrict__ acc,
+                                                                 const double *__restrict__ dtp,
+                                                                 int *__restrict__ status, int rows)
+{
+    extern __shared__ __align__(16) float smem[];
+    __shared__ UpdC uc;
+    fused2d_strip<STAGE, NS, TX, NT>(P, fused_geo(P), s0, s1, W, acc, dtp[0], status, blockIdx.x * TX,
+                                     blockIdx.y * rows, rows, smem, uc);
 }
 
 } // namespace gks

@@ -2,6 +2,7 @@
  * list (grid-stride over tiles), every thread walks the items of its tile.
  * The per-item arithmetic is the single-grid kernels' (kernels.cuh). */
 #include "batch.h"
+#include "fused2d.cuh"
 
 namespace gks {
 
@@ -117,6 +118,64 @@ __global__ void __launch_bounds__(256) bk_update(const GridDesc *__restrict__ gd
     }
 }
 
+/* Mixed precision: one stage of every grid in one launch.  Block b runs the
+ * fused reconstruction -> flux -> update sweep (fused2d_strip) of strip b of
+ * the list.  The grids share every scheme constant and boundary type, so the
+ * kernel takes one parameter block (its geometry fields unused) as a launch
+ * parameter, and per strip only the grid's geometry, state pointers and time
+ * step.  Measured on the 256-grid workload (2D, sides 64..1024): one block
+ * per strip at 2 blocks per SM (128 registers, no spills) 1.14 G
+ * cell-updates/s; a persistent grid-stride loop over the strips at 3 blocks
+ * per SM (80 registers, 220 bytes of spills) 0.95 G, at 2 blocks per SM
+ * 1.06 G; one block per strip at 3 blocks per SM 1.05 G. */
+constexpr int kStageThreads = 256, kStageMinBlocks = 2;
+
+template <int STAGE>
+__global__ void __launch_bounds__(kStageThreads, kStageMinBlocks)
+    bk_stage(const KP P, const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, const double *__restrict__ dt,
+             int *__restrict__ status)
+{
+    extern __shared__ __align__(16) float smem[];
+    __shared__ UpdC uc;
+    const Tile T = tiles[blockIdx.x];
+    const GridDesc &g = gd[T.grid];
+    const FusedGeo geo{g.P.n[0], g.P.n[1], g.P.ncell, g.P.ih, g.P.fh, g.P.fih};
+    /* the shadows' lo and g planes follow hi at 4 and 8 planes of cells */
+    const long nc = geo.nc;
+    float *const h0 = g.s0.hi, *const h1 = g.s1.hi;
+    const Shadow s0{h0, h0 + 4 * nc, h0 + 8 * nc}, s1{h1, h1 + 4 * nc, h1 + 8 * nc};
+    fused2d_strip<STAGE, false, kStageStrip, kStageThreads>(P, geo, s0, s1, g.W, (float *)g.Acc, dt[T.grid], status,
+                                                           T.kind, (int)T.begin, (int)(T.end - T.begin), smem, uc);
+}
+
+/* the dynamic shared memory opt-in of both stage kernels, once */
+cudaError_t stage_prepare()
+{
+    using Strip = SweepStrip<kStageStrip>;
+    static const cudaError_t prep = [] {
+        cudaError_t e = cudaFuncSetAttribute(bk_stage<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Strip::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bk_stage<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Strip::SMEM);
+        for (auto k : {bk_stage<1>, bk_stage<2>})
+            if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+                (void)cudaGetLastError();
+        return e;
+    }();
+    return prep;
+}
+
+cudaError_t batch_stage(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st)
+{
+    using Strip = SweepStrip<kStageStrip>;
+    const cudaError_t prep = stage_prepare();
+    if (prep != cudaSuccess) return prep;
+    if (S.block != kStageThreads) return cudaErrorInvalidConfiguration;
+    if (L.ntiles < 1) return cudaSuccess;
+    if (stage == 1) bk_stage<1><<<L.ntiles, kStageThreads, Strip::SMEM, st>>>(*L.common, L.gd, L.tiles, L.dt, L.status);
+    else bk_stage<2><<<L.ntiles, kStageThreads, Strip::SMEM, st>>>(*L.common, L.gd, L.tiles, L.dt, L.status);
+    return cudaGetLastError();
+}
+
 template <typename R> cudaError_t batch_speed(const BatchLaunch &L, const LaunchShape &S, cudaStream_t st)
 {
     bk_speed<R><<<S.blocks, S.block, 0, st>>>(L.gd, L.tiles, L.ntiles, L.smax);
@@ -168,17 +227,21 @@ int batch_occupancy(int kernel, int precision, int block)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_speed<float> : bk_speed<double>, block, 0);
         break;
     case BK_POLY:
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_poly<float> : bk_poly<double>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bk_poly<double>, block, 0);
         break;
     case BK_FLUX:
-        /* its coefficient staging needs a larger shared-memory carveout than
-         * the default to reach the launch bounds' blocks per SM */
-        if (precision) smem_carveout_for(bk_flux<float>, flux_blocks_per_sm<float, 2, false>());
-        else smem_carveout_for(bk_flux<double>, flux_blocks_per_sm<double, 2, false>());
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_flux<float> : bk_flux<double>, block, 0);
+        smem_carveout_for(bk_flux<double>, flux_blocks_per_sm<double, 2, false>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bk_flux<double>, block, 0);
+        break;
+    case BK_STAGE:
+        /* the opt-in to the dynamic shared memory, then the occupancy with it */
+        if (stage_prepare() == cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bk_stage<1>, kStageThreads, SweepStrip<kStageStrip>::SMEM);
+        else
+            (void)cudaGetLastError();
         break;
     default:
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? bk_update<float> : bk_update<double>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bk_update<double>, block, 0);
         break;
     }
     return n;
@@ -189,7 +252,7 @@ int batch_occupancy(int kernel, int precision, int block)
     template cudaError_t batch_poly<R>(const BatchLaunch &, const LaunchShape &, int, cudaStream_t);   \
     template cudaError_t batch_flux<R>(const BatchLaunch &, const LaunchShape &, int, cudaStream_t);   \
     template cudaError_t batch_update<R>(const BatchLaunch &, const LaunchShape &, int, cudaStream_t);
-GKS_BATCH_INST(float)
+template cudaError_t batch_speed<float>(const BatchLaunch &, const LaunchShape &, cudaStream_t);
 GKS_BATCH_INST(double)
 
 } // namespace gks

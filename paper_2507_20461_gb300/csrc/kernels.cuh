@@ -1045,16 +1045,16 @@ __device__ __forceinline__ long face_of(const KP &P, int d, int i, int j, int k,
  * and re-splits W into s0, so the shadow never drifts from W.  The sums of
  * the averages are conserved to FP64 rounding.  Gradients (not conserved)
  * come from FP32 differences of the interface states and live in the shadow
- * only (Eq. slope).  mixed_update_var updates variable v and returns its new
- * FP32 value; mixed_update_cell all variables and the admissibility flags. */
+ * only (Eq. slope).  mixed_update_var updates variable v (nc cells, fih =
+ * 1/h in FP32) and returns its new FP32 value; mixed_update_cell all
+ * variables and the admissibility flags. */
 template <int M, int STAGE, typename FaceSum>
-__device__ __forceinline__ float mixed_update_var(const KP &P, const FaceSum &fsum, const UpdC &uc,
+__device__ __forceinline__ float mixed_update_var(long nc, float fih, const FaceSum &fsum, const UpdC &uc,
                                                  double *__restrict__ W, float *__restrict__ acc, const Shadow &s0,
                                                  const Shadow &s1, long cell, int v)
 {
     constexpr int NV = M + 2, NG = (M == 2) ? 2 : 4;
-    const long nc = P.ncell;
-    const float gw = P.fih / NG;
+    const float gw = fih / NG;
     const Shadow &so = (STAGE == 1) ? s1 : s0;
     float sF = 0.f, eF = 0.f, sT = 0.f, eT = 0.f;
 #pragma unroll
@@ -1109,7 +1109,7 @@ __device__ __forceinline__ void mixed_update_cell(const KP &P, const FaceSum &fs
     constexpr int NV = M + 2;
     float wn[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) wn[v] = mixed_update_var<M, STAGE>(P, fsum, uc, W, acc, s0, s1, cell, v);
+    for (int v = 0; v < NV; ++v) wn[v] = mixed_update_var<M, STAGE>(P.ncell, P.fih, fsum, uc, W, acc, s0, s1, cell, v);
     mixed_state_flags<M>(P, wn, status);
 }
 

@@ -104,6 +104,17 @@ def main():
         two = {k: 2 * flx[k] for k in ("add", "mul", "div") + TRANS}
         out[f"update_cell_stage_{dim}d"] = diff(stp, two, 2 * cells)
         out[f"grid_{dim}d"] = {"n": n, "cells": cells, "unique_gauss_points": ngp, "seed": 7 + dim}
+    # 1D non-compact GENO (order 5 / 6), HLLC, classical RK4: one step of a
+    # smooth periodic grid, per cell-update (the face kernel evaluates each
+    # face once per RK stage)
+    n = 64
+    W1, _, h1 = smooth_state(1, n, 5)
+    cfg1 = O.make_cfg(1, (n,), h1, bc=0)
+    dt1 = 0.4 * h1 / O.max_wavespeed(cfg1, W1)
+    for order in (5, 6):
+        r = opcount.nc_step(order, n, h1, dt1, W1)
+        assert r["status"] == 0
+        out[f"nc_step_cell_update_1d_order{order}"] = summary(r, n)
     with open(OUT, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
         f.write("\n")
