@@ -71,14 +71,18 @@ CELL_UPDATE_2D_LIMITER = {lim: CELL_UPDATE_2D + 2 * 4 * (_flops(f"cubic_cell_var
 # 1D non-compact GENO + HLLC, one classical RK4 step (4 stages)
 NC_CELL_UPDATE = {o: _flops(f"nc_step_cell_update_1d_order{o}") for o in (5, 6)}
 # Executed flops of the face-flux kernel itself (ncu: 2 x FMA + ADD + MUL of
-# the pipe, per face Gauss point, on a 256^2 case where every point is
-# evaluated once; the face-flux flop summary under profiles/).  The kernel
-# uses closed forms where the oracle solves moment systems, so it executes
-# fewer flops than the algorithmic count.
-EXECUTED_FLOPS_PER_FACE_GP = {"mixed": None, "fp64": None}
-# DRAM bytes (read + write) per launch of the face-flux kernel from a 1-pass
-# ncu capture (None until captured for the current kernel).
-TRAFFIC_PER_FLUX_LAUNCH = {"mixed": None, "fp64": None}
+# the pipe, per face Gauss point, on a 256^2 case whose index space is whole
+# 128-item groups, so every point is evaluated exactly once; mean of the four
+# launches of a step; the face-flux flop summary under profiles/).  The
+# kernel uses closed forms where the oracle solves moment systems, so it
+# executes fewer flops than the algorithmic count.
+EXECUTED_FLOPS_PER_FACE_GP = {"mixed": 1686.2, "fp64": 1908.1}
+# DRAM bytes (read + write) per launch of the face-flux kernel: the mean of
+# the four launches of a 1-pass ncu capture at 1024^2 (coefficients 151 MB
+# FP32 / 303 MB FP64, above L2): 202.4 MB mixed, 854.7 MB FP64, scaled to
+# the 2048^2 launch by the Gauss points it processes.
+TRAFFIC_PER_FLUX_LAUNCH = {"mixed": 202.43e6 * (2049 * 2048) / (1025 * 1024),
+                           "fp64": 854.69e6 * (2049 * 2048) / (1025 * 1024)}
 # Algorithmic HBM bytes per cell-update of the whole step (FP64 state,
 # stage buffers, accumulator), 2D: 60 doubles.
 BYTES_PER_CELL_UPDATE = 480.0
