@@ -15,7 +15,13 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgenogks.so")
 SOURCES = ["k1d.cu", "k2d.cu", "k3d.cu", "k2d_batch.cu", "k2d_fused.cu", "api.cu", "batch.cu", "static_flux.cu", "analysis.cu", "probe.cu", "k1d_nc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# FP32 division and square root compile to the approximate forms (at most 2
+# and about 1 ulp off; FP64 code is unaffected): the mixed-precision flux and
+# reconstruction issue fewer instructions and the 2048^2 step is 4% shorter,
+# the fused stage kernel 9%.  Denormals are kept (flushing them slowed the
+# double-float update).
+FLAGS = ["-std=c++17", "-O3", "-prec-div=false", "-prec-sqrt=false", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
+         "-O2"]
 
 
 def nvcc() -> str:
