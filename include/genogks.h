@@ -330,10 +330,10 @@ int gks_batch_set_state(gks_batch_t b, int grid, const double *W, const double *
 int gks_batch_get_state(gks_batch_t b, int grid, double *W, double *G, int on_device);
 
 /* nsteps steps of every grid, grid b with dt_b = cfl h_b / (its max |u_d| + c)
- * computed on the device.  Mixed precision: per stage one launch of the
- * fused stage kernel (reconstruction, flux and update through shared
- * memory), one block per strip of a list spanning every grid; FP64: per
- * stage three
+ * computed on the device.  Mixed precision: per stage one persistent launch
+ * of the fused stage kernel (reconstruction, flux and update through shared
+ * memory), its blocks taking strips of a list spanning every grid from a
+ * work counter; FP64: per stage three
  * persistent kernels (per-cell reconstruction, face flux, update) walk tile
  * lists spanning all grids.  The first call picks the tile sizes (rows per
  * strip) and block sizes by timing candidates (an autotuner; only scratch

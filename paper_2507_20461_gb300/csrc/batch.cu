@@ -2,8 +2,8 @@
  * uneven sizes, persistent kernels over tile work lists, per-grid time steps
  * on the device, one step captured into a CUDA graph and replayed.  Mixed
  * precision runs each stage as one persistent launch of the fused stage
- * kernel over a list of strips of every grid (one block per strip); FP64
- * runs the three kernel
+ * kernel over a list of strips of every grid (persistent blocks take the
+ * strips from a work counter); FP64 runs the three kernel
  * classes (reconstruction, flux, update).  The tile size and block size of
  * every kernel class are picked by timing the candidates on the actual grids
  * before the graph is recorded; the choices are cached per (dimension,
@@ -136,6 +136,12 @@ void stage_tiles(const gks_batch_ctx *b, long rows, std::vector<Tile> &v)
         for (int x0 = 0; x0 < P.n[0]; x0 += gks::kStageStrip)
             for (long y0 = 0; y0 < P.n[1]; y0 += rows) v.push_back(Tile{g, x0, y0, y0 + rows < P.n[1] ? y0 + rows : P.n[1]});
     }
+    /* largest strips first (columns x rows), so the work counter ends on small ones */
+    auto cost = [b](const Tile &t) {
+        const int w = std::min(gks::kStageStrip, b->hd[t.grid].P.n[0] - t.kind);
+        return (long)w * (t.end - t.begin);
+    };
+    std::stable_sort(v.begin(), v.end(), [&](const Tile &a, const Tile &c) { return cost(a) > cost(c); });
 }
 
 int build_tiles(gks_batch_ctx *b, int k, long tile)
@@ -168,7 +174,7 @@ int build_tiles(gks_batch_ctx *b, int k, long tile)
 
 BatchLaunch launch_of(gks_batch_ctx *b, int k)
 {
-    return BatchLaunch{b->dd, b->tiles[k], b->ntiles[k], b->dt, b->smax, b->status, &b->hd[0].P};
+    return BatchLaunch{b->dd, b->tiles[k], b->ntiles[k], b->dt, b->smax, b->status, &b->hd[0].P, b->status + 4};
 }
 
 cudaError_t run_class(gks_batch_ctx *b, int k, int stage)

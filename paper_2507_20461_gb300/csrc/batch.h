@@ -43,13 +43,15 @@ struct BatchLaunch {
     unsigned long long *smax;   /* per grid */
     int *status;
     const KP *common;           /* host: the scheme constants every grid shares */
+    int *queue;                 /* device: work counters of the fused stage kernel (one per stage) */
 };
 
 template <typename R> cudaError_t batch_speed(const BatchLaunch &L, const LaunchShape &S, cudaStream_t st);
 template <typename R> cudaError_t batch_poly(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st);
 template <typename R> cudaError_t batch_flux(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st);
 template <typename R> cudaError_t batch_update(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st);
-/* mixed precision: one stage of every grid as one fused kernel over strips */
+/* mixed precision: one stage of every grid as one persistent fused kernel
+ * over a strip list (a work counter hands out the strips) */
 cudaError_t batch_stage(const BatchLaunch &L, const LaunchShape &S, int stage, cudaStream_t st);
 cudaError_t batch_dt(const GridDesc *gd, int nb, double cfl, const unsigned long long *smax, double *dt, cudaStream_t st);
 cudaError_t batch_shadow(const GridDesc &g, cudaStream_t st);

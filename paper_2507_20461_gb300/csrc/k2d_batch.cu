@@ -118,34 +118,40 @@ __global__ void __launch_bounds__(256) bk_update(const GridDesc *__restrict__ gd
     }
 }
 
-/* Mixed precision: one stage of every grid in one launch.  Block b runs the
- * fused reconstruction -> flux -> update sweep (fused2d_strip) of strip b of
- * the list.  The grids share every scheme constant and boundary type, so the
- * kernel takes one parameter block (its geometry fields unused) as a launch
- * parameter, and per strip only the grid's geometry, state pointers and time
- * step.  Measured on the 256-grid workload (2D, sides 64..1024): one block
- * per strip at 2 blocks per SM (128 registers, no spills) 1.14 G
- * cell-updates/s; a persistent grid-stride loop over the strips at 3 blocks
- * per SM (80 registers, 220 bytes of spills) 0.95 G, at 2 blocks per SM
- * 1.06 G; one block per strip at 3 blocks per SM 1.05 G. */
+/* Mixed precision: one stage of every grid in one persistent launch.  Each
+ * block takes the next strip of the list from a work counter (strips ordered
+ * by size, largest first) and runs the fused reconstruction -> flux ->
+ * update sweep (fused2d_strip) of it, until the list is done.  The grids
+ * share every scheme constant and boundary type, so the kernel takes one
+ * parameter block (its geometry fields unused) as a launch parameter, and
+ * per strip only the grid's geometry, state pointers and time step. */
 constexpr int kStageThreads = 256, kStageMinBlocks = 2;
 
 template <int STAGE>
 __global__ void __launch_bounds__(kStageThreads, kStageMinBlocks)
-    bk_stage(const KP P, const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, const double *__restrict__ dt,
-             int *__restrict__ status)
+    bk_stage(const KP P, const GridDesc *__restrict__ gd, const Tile *__restrict__ tiles, int ntiles,
+             const double *__restrict__ dt, int *__restrict__ queue, int *__restrict__ status)
 {
     extern __shared__ __align__(16) float smem[];
     __shared__ UpdC uc;
-    const Tile T = tiles[blockIdx.x];
-    const GridDesc &g = gd[T.grid];
-    const FusedGeo geo{g.P.n[0], g.P.n[1], g.P.ncell, g.P.ih, g.P.fh, g.P.fih};
-    /* the shadows' lo and g planes follow hi at 4 and 8 planes of cells */
-    const long nc = geo.nc;
-    float *const h0 = g.s0.hi, *const h1 = g.s1.hi;
-    const Shadow s0{h0, h0 + 4 * nc, h0 + 8 * nc}, s1{h1, h1 + 4 * nc, h1 + 8 * nc};
-    fused2d_strip<STAGE, false, kStageStrip, kStageThreads>(P, geo, s0, s1, g.W, (float *)g.Acc, dt[T.grid], status,
-                                                           T.kind, (int)T.begin, (int)(T.end - T.begin), smem, uc);
+    __shared__ int next;
+    for (;;) {
+        __syncthreads(); /* every thread has read `next`; the previous strip is done with uc and the rings */
+        if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int ti = next;
+        if (ti >= ntiles) break;
+        const Tile T = tiles[ti];
+        const GridDesc &g = gd[T.grid];
+        const FusedGeo geo{g.P.n[0], g.P.n[1], g.P.ncell, g.P.ih, g.P.fh, g.P.fih};
+        /* the shadows' lo and g planes follow hi at 4 and 8 planes of cells */
+        const long nc = geo.nc;
+        float *const h0 = g.s0.hi, *const h1 = g.s1.hi;
+        const Shadow s0{h0, h0 + 4 * nc, h0 + 8 * nc}, s1{h1, h1 + 4 * nc, h1 + 8 * nc};
+        fused2d_strip<STAGE, false, kStageStrip, kStageThreads>(P, geo, s0, s1, g.W, (float *)g.Acc, dt[T.grid],
+                                                               status, T.kind, (int)T.begin, (int)(T.end - T.begin),
+                                                               smem, uc);
+    }
 }
 
 /* the dynamic shared memory opt-in of both stage kernels, once */
@@ -171,8 +177,13 @@ cudaError_t batch_stage(const BatchLaunch &L, const LaunchShape &S, int stage, c
     if (prep != cudaSuccess) return prep;
     if (S.block != kStageThreads) return cudaErrorInvalidConfiguration;
     if (L.ntiles < 1) return cudaSuccess;
-    if (stage == 1) bk_stage<1><<<L.ntiles, kStageThreads, Strip::SMEM, st>>>(*L.common, L.gd, L.tiles, L.dt, L.status);
-    else bk_stage<2><<<L.ntiles, kStageThreads, Strip::SMEM, st>>>(*L.common, L.gd, L.tiles, L.dt, L.status);
+    int *q = L.queue + (stage - 1);
+    cudaError_t e = cudaMemsetAsync(q, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (stage == 1)
+        bk_stage<1><<<S.blocks, kStageThreads, Strip::SMEM, st>>>(*L.common, L.gd, L.tiles, L.ntiles, L.dt, q, L.status);
+    else
+        bk_stage<2><<<S.blocks, kStageThreads, Strip::SMEM, st>>>(*L.common, L.gd, L.tiles, L.ntiles, L.dt, q, L.status);
     return cudaGetLastError();
 }
 
