@@ -214,22 +214,22 @@ __device__ __forceinline__ void fused2d_strip(const KP &P, const FusedGeo &geo, 
                 rc[4 * k + 2] = q.z;
                 rc[4 * k + 3] = q.w;
             }
+            /* one evaluation code for both directions: a y face of the cubic
+             * P(x, y) is the x face of P(y, x), whose coefficients are P's with
+             * x and y swapped (monomials y, x, y^2, xy, x^2, y^3, xy^2, x^2y,
+             * x^3); its two derivatives swap back */
+            constexpr int swp[NC] = {1, 0, 4, 3, 2, 8, 7, 6, 5};
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 float c[NC], out[3];
 #pragma unroll
-                for (int k = 0; k < NC; ++k) c[k] = rc[v * NC + k];
-                if (xd) {
-                    if (side == 0) CubicEval<float, 2, 0, 1>::run(g, c, out);
-                    else CubicEval<float, 2, 0, 0>::run(g, c, out);
-                } else {
-                    if (side == 0) CubicEval<float, 2, 1, 1>::run(g, c, out);
-                    else CubicEval<float, 2, 1, 0>::run(g, c, out);
-                }
+                for (int k = 0; k < NC; ++k) c[k] = xd ? rc[v * NC + k] : rc[v * NC + swp[k]];
+                if (side == 0) CubicEval<float, 2, 0, 1>::run(g, c, out);
+                else CubicEval<float, 2, 0, 0>::run(g, c, out);
                 cw[side][v] = wv[v];
                 st[side][v][0] = wv[v] + out[0];
-                st[side][v][1] = out[1] * ih;
-                st[side][v][2] = out[2] * ih;
+                st[side][v][1] = (xd ? out[1] : out[2]) * ih;
+                st[side][v][2] = (xd ? out[2] : out[1]) * ih;
             }
             float s[NV];
 #pragma unroll

@@ -94,9 +94,36 @@ def test_fused_equals_three_kernel_path_per_side(sides):
     _agree(a, b, W, h)
 
 
+def _smooth_exact(nx, ny, seed):
+    """A smooth periodic state with its exact cell-averaged gradients (the
+    point values and derivatives at cell centres): no weight sits at a cut."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / max(nx, ny)
+    y, x = np.meshgrid((np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx, indexing="ij")
+    a = rng.uniform(0, 2 * np.pi)
+    k = 2 * np.pi
+    ph = k * (x + y) + a
+    rho, drho = 1 + 0.2 * np.sin(ph), 0.2 * np.cos(ph)
+    u, du = 0.3 * np.cos(ph), -0.3 * np.sin(ph)
+    v, dv = 0.2 * np.sin(ph), 0.2 * np.cos(ph)
+    p, dp = 1 + 0.1 * np.cos(ph), -0.1 * np.sin(ph)
+    W = np.stack([rho, rho * u, rho * v, p / 0.4 + 0.5 * rho * (u * u + v * v)])
+    dW = np.stack([drho, drho * u + rho * du, drho * v + rho * dv,
+                   dp / 0.4 + 0.5 * drho * (u * u + v * v) + rho * (u * du + v * dv)])
+    G = np.stack([k * dW, k * dW])  # d/dx = d/dy = k d/dph
+    return W, G, 1.0 / nx
+
+
 @pytest.mark.parametrize("limiter", [1, 2, 3])
 def test_fused_equals_three_kernel_path_limiters(limiter):
-    W, G, h = _state(45, 38, 7 + limiter)
+    """GENO (tested above), the linear scheme and WENO-Z on a noisy state;
+    TENO on a smooth state with exact gradients, because its cut is a switch:
+    on noisy data a rounding-level difference between the two kernels can
+    drop a candidate in one and keep it in the other."""
+    if limiter == 3:
+        W, G, h = _smooth_exact(48, 48, 11)
+    else:
+        W, G, h = _state(45, 38, 7 + limiter)
     a = _run(W, G, h, 5, 1, limiter=limiter)
     b = _run(W, G, h, 5, 0, limiter=limiter)
     _agree(a, b, W, h)
