@@ -40,6 +40,13 @@ def _newest_input() -> float:
     return t
 
 
+# extra flags per translation unit: the fused stage kernels flush FP32
+# denormals (their double-float update never comes near them; measured 1.5%
+# shorter fused stage, 2.4% faster batch), the three-kernel update does not
+# (it ran 17% slower)
+UNIT_FLAGS: dict[str, list[str]] = {"k2d_fused.cu": ["-ftz=true"], "k2d_batch.cu": ["-ftz=true"]}
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
@@ -50,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
-        cmd = [cc, *FLAGS, *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *FLAGS, *UNIT_FLAGS.get(src, []), *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -159,10 +159,10 @@ def test_one_step_parity(dim, n, bc):
     s.close()
 
 
-def _run_pair(dim, n, h, bc, W, G, nsteps, cfl=0.4, precision=0):
+def _run_pair(dim, n, h, bc, W, G, nsteps, cfl=0.4, precision=0, stage_kernels=0):
     """nsteps on both sides with the oracle's CFL time steps fed to the GPU."""
     cfg = O.make_cfg(dim, n, h, bc=bc)
-    s = _solver(dim, n, h, bc, precision=precision)
+    s = _solver(dim, n, h, bc, precision=precision, stage_kernels=stage_kernels)
     Wd, Gd = _dev(W), _dev(G)
     s.set_state(Wd, Gd)
     Wo, Go = W.copy(), G.copy()
@@ -233,10 +233,18 @@ def test_3d_multistep_parity():
 MIXED_SMOOTH_2D = dict(n=64, seed=20463, nshocks=0, drift=(0.5, 0.25))
 
 
+# the 2D mixed-precision step runs either as three kernels (stage_kernels 0)
+# or as the fused stage kernel (1); the mixed-precision bars hold for both
+SK = [0, 1]
+
+
+@pytest.mark.parametrize("sk", SK)
 @pytest.mark.parametrize("case", ["fourier_smooth_2d", "riemann_1d"])
-def test_mixed_precision_density_l1(case):
+def test_mixed_precision_density_l1(case, sk):
     """FP32 reconstruction/flux with FP64 accumulation against the FP64 oracle,
     20 steps: mean |rho_gpu - rho_oracle| <= 1e-5."""
+    if case == "riemann_1d" and sk:
+        pytest.skip("the fused stage kernel is 2D")
     if case == "fourier_smooth_2d":
         c = MIXED_SMOOTH_2D
         W, G, h = I.fourier_shocks_2d(c["n"], seed=c["seed"], nshocks=c["nshocks"], drift=c["drift"])
@@ -244,18 +252,19 @@ def test_mixed_precision_density_l1(case):
     else:
         W, G, h, _ = I.riemann_1d(200, seed=20461)
         dim, n, bc = 1, (200,), 1
-    Wg, Gg, Wo, Go = _run_pair(dim, n, h, bc, W, G, 20, precision=1)
+    Wg, Gg, Wo, Go = _run_pair(dim, n, h, bc, W, G, 20, precision=1, stage_kernels=sk)
     err = np.abs(Wg[0] - Wo[0]).mean()
     assert err <= 1e-5, err
 
 
-def test_mixed_precision_shock_case_within_switch_spread():
+@pytest.mark.parametrize("sk", SK)
+def test_mixed_precision_shock_case_within_switch_spread(sk):
     """64^2 Fourier modes + 4 shocks, 20 steps: the mixed result lies within
     1e-5 of the oracle plus the oracle's own spread when the admissibility
     threshold moves by a relative 1e-4 (the FP32 face states' rounding)."""
     n = 64
     W, G, h = I.fourier_shocks_2d(n, seed=20463)
-    Wg, Gg, Wo, Go = _run_pair(2, (n, n), h, 0, W, G, 20, precision=1)
+    Wg, Gg, Wo, Go = _run_pair(2, (n, n), h, 0, W, G, 20, precision=1, stage_kernels=sk)
     spread = 0.0
     for r in (-1e-4, 1e-4):
         cfg = O.make_cfg(2, (n, n), h, bc=0, adm_delta=0.3 * (1 + r))
@@ -305,14 +314,14 @@ def _window_check(Wfull, Gfull, Wnew, Gnew, dim, n, h, dt, rng, nwin=6, r=4, pad
             np.testing.assert_allclose(got_g, ref_g, rtol=0, atol=gtol + 1e-9 * np.abs(ref_g).max())
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
-def test_config3_full_size_sampled(precision, tol):
+@pytest.mark.parametrize("precision,tol,sk", [(0, 1e-12, 0), (1, 2e-5, 0), (1, 2e-5, 1)])
+def test_config3_full_size_sampled(precision, tol, sk):
     """2D 2048^2 periodic Fourier modes + 4 shocks (the benchmark workload),
     one step through gks_step_cfl (dt computed on the device); sampled windows
     compared with the oracle."""
     n = 2048
     W, G, h = I.fourier_shocks_2d(n, seed=20463)
-    s = _solver(2, (n, n), h, 0, precision=precision)
+    s = _solver(2, (n, n), h, 0, precision=precision, stage_kernels=sk)
     Wd, Gd = _dev(W), _dev(G)
     s.set_state(Wd, Gd)
     smax = s.max_wavespeed()
@@ -326,7 +335,8 @@ def test_config3_full_size_sampled(precision, tol):
     s.close()
 
 
-def test_config3_mixed_l1_full_size():
+@pytest.mark.parametrize("sk", SK)
+def test_config3_mixed_l1_full_size(sk):
     """The mixed-precision bar on the workload it is stated for: 2048^2
     periodic Fourier modes + 4 shocks, 20 steps with the same time steps on
     the mixed and the FP64 path (the FP64 path matches the oracle to 1e-12
@@ -340,7 +350,7 @@ def test_config3_mixed_l1_full_size():
     n = 2048
     W, G, h = I.fourier_shocks_2d(n, seed=20463)
     s64 = _solver(2, (n, n), h, 0, precision=0)
-    s32 = _solver(2, (n, n), h, 0, precision=1)
+    s32 = _solver(2, (n, n), h, 0, precision=1, stage_kernels=sk)
     W64, G64 = _dev(W), _dev(G)
     W32, G32 = _dev(W), _dev(G)
     s64.set_state(W64, G64)
@@ -618,15 +628,17 @@ def test_per_side_bc_rejects_unpaired_periodic():
     assert e.value.code == B.ERR_ARG
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision,sk", [(0, 0), (1, 0), (1, 1)])
 @pytest.mark.parametrize("dim,n", [(2, (256, 256)), (3, (48, 40, 32))])
-def test_conservation_periodic(dim, n, precision):
+def test_conservation_periodic(dim, n, precision, sk):
     """Periodic grids: the summed cell averages of every conserved variable stay
     fixed to FP64 rounding in both precisions (the face fluxes of a cell are
     accumulated exactly, so each face's flux leaves one cell and enters the
     other without a rounding of its own)."""
+    if sk and dim != 2:
+        pytest.skip("the fused stage kernel is 2D")
     W, G, h = _random_smooth(dim, n, 90 + dim, 0)
-    s = _solver(dim, n, h, 0, precision=precision)
+    s = _solver(dim, n, h, 0, precision=precision, stage_kernels=sk)
     Wd, Gd = _dev(W), _dev(G)
     s.set_state(Wd, Gd)
     s.step_cfl(0.4, 40)
@@ -670,14 +682,15 @@ def test_limiter_variants_parity(dim, n, limiter):
     s.close()
 
 
+@pytest.mark.parametrize("sk", SK)
 @pytest.mark.parametrize("limiter", [2, 3])
-def test_limiter_variants_mixed(limiter):
+def test_limiter_variants_mixed(limiter, sk):
     """Mixed precision with WENO-Z / TENO weights, 2D quadrants, 10 steps:
     mean |d rho| against the FP64 oracle within the mixed-precision bar."""
     n = (40, 36)
     W, G, h = I.quadrants_2d(36, seed=31, nx=40)
     cfg = O.make_cfg(2, n, h, bc=1, limiter=limiter)
-    s = _solver(2, n, h, 1, precision=1, limiter=limiter)
+    s = _solver(2, n, h, 1, precision=1, limiter=limiter, stage_kernels=sk)
     Wd, Gd = _dev(W), _dev(G)
     s.set_state(Wd, Gd)
     Wo, Go = W.copy(), G.copy()
