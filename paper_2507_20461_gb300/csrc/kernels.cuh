@@ -22,6 +22,7 @@
 #pragma once
 #include <cstdint>
 
+#include "fpsplit.cuh"
 #include "geno_coeffs.cuh"
 #include "gks_device.cuh"
 
@@ -149,9 +150,10 @@ template <> struct Src<float> {
 
 __device__ __forceinline__ void split_store(double w, float *hi, float *lo, long i)
 {
-    const float a = (float)w;
+    float a, b;
+    split(w, a, b);
     hi[i] = a;
-    lo[i] = (float)(w - (double)a);
+    lo[i] = b;
 }
 
 /* Mirror bits of one crossing of a wall of type t (ghost cells are mirror
@@ -1080,10 +1082,13 @@ __device__ __forceinline__ float mixed_update_var(long nc, float fih, const Face
         return w.hi;
     } else {
         const F2 dW = df_add(F2{acc[v * nc + cell], acc[(NV + v) * nc + cell]}, df_mul(uc.k[4], ST));
-        const double w = (W[v * nc + cell] + (double)dW.hi) + (double)dW.lo;
+        const double w = (W[v * nc + cell] + widen(dW.hi)) + widen(dW.lo);
         W[v * nc + cell] = w;
-        split_store(w, so.hi, so.lo, v * nc + cell);
-        return (float)w;
+        float wh, wl;
+        split(w, wh, wl);
+        so.hi[v * nc + cell] = wh;
+        so.lo[v * nc + cell] = wl;
+        return wh;
     }
 }
 
