@@ -234,7 +234,8 @@ int gks_profile_read(gks_handle_t h, int kernel_class, long *launches, double *m
  * denominator of the stage kernels' rooflines (the paper has no
  * counterpart: measurement infrastructure).  kind 0: FP32 fused multiply-add
  * (2 flops each), 1: FP64 fused multiply-add, 2: the FP32 special-function
- * unit (ex2.approx, 1 op each).  A grid of 8 blocks of 256 threads per SM
+ * unit (ex2.approx, 1 op each), 3: FP32 fused multiply-add issued as packed
+ * two-lane instructions (fma.rn.f32x2, 4 flops each).  A grid of 8 blocks of 256 threads per SM
  * runs iters x 32 operations per thread on eight independent chains; the
  * second of two launches is timed with CUDA events on `stream` (NULL = the
  * legacy default stream), which the call synchronises.  *ops_per_s receives

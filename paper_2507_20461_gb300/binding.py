@@ -436,12 +436,13 @@ class Solver:
             pass
 
 
-PIPE_FFMA, PIPE_DFMA, PIPE_MUFU = 0, 1, 2
+PIPE_FFMA, PIPE_DFMA, PIPE_MUFU, PIPE_FFMA2 = 0, 1, 2, 3
 
 
 def pipe_probe(kind: int, iters: int, stream=None) -> float:
     """Measured throughput (flops or ops per second) of one arithmetic pipe:
-    PIPE_FFMA, PIPE_DFMA (2 flops per FMA) or PIPE_MUFU (1 op per ex2)."""
+    PIPE_FFMA, PIPE_DFMA (2 flops per FMA), PIPE_MUFU (1 op per ex2) or
+    PIPE_FFMA2 (packed two-lane FP32 FMA, 4 flops per instruction)."""
     out = C.c_double()
     sp = _stream_ptr(stream)
     _check(None, lib().gks_pipe_probe(int(kind), int(iters), C.byref(out), sp))

@@ -44,6 +44,27 @@ __global__ void __launch_bounds__(256) dfma_probe(double *out, int iters, double
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+/* the same FMA work as ffma_probe, issued as packed two-lane FMAs
+ * (fma.rn.f32x2): one instruction per pair of chains */
+__global__ void __launch_bounds__(256) ffma2_probe(float *out, int iters, float a, float b)
+{
+    float2 x[kChains / 2];
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k)
+        x[k] = make_float2(1e-3f * (float)(threadIdx.x + 2 * k), 1e-3f * (float)(threadIdx.x + 2 * k + 1));
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < kChains / 2; ++k) x[k] = __ffma2_rn(x[k], a2, b2);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChains / 2; ++k) s += x[k].x + x[k].y;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 /* the special-function unit: x <- 2^-x (ex2.approx, the instruction behind
  * the FP32 exponentials), bounded in (0, 1] */
 __global__ void __launch_bounds__(256) mufu_probe(float *out, int iters)
@@ -71,7 +92,7 @@ __global__ void __launch_bounds__(256) mufu_probe(float *out, int iters)
 
 extern "C" int gks_pipe_probe(int kind, int iters, double *ops_per_s, void *stream)
 {
-    if (!ops_per_s || iters < 1 || kind < 0 || kind > 2) return GKS_ERR_ARG;
+    if (!ops_per_s || iters < 1 || kind < 0 || kind > 3) return GKS_ERR_ARG;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return GKS_ERR_CUDA;
@@ -86,7 +107,8 @@ extern "C" int gks_pipe_probe(int kind, int iters, double *ops_per_s, void *stre
     auto launch = [&](int it) {
         if (kind == 0) ffma_probe<<<blocks, threads, 0, s>>>((float *)buf, it, 0.9999f, 1e-4f);
         else if (kind == 1) dfma_probe<<<blocks, threads, 0, s>>>((double *)buf, it, 0.9999, 1e-4);
-        else mufu_probe<<<blocks, threads, 0, s>>>((float *)buf, it);
+        else if (kind == 2) mufu_probe<<<blocks, threads, 0, s>>>((float *)buf, it);
+        else ffma2_probe<<<blocks, threads, 0, s>>>((float *)buf, it, 0.9999f, 1e-4f);
     };
     launch(iters); /* warm-up */
     cudaEventRecord(e0, s);
