@@ -71,12 +71,12 @@ CELL_UPDATE_2D_LIMITER = {lim: CELL_UPDATE_2D + 2 * 4 * (_flops(f"cubic_cell_var
 # 1D non-compact GENO + HLLC, one classical RK4 step (4 stages)
 NC_CELL_UPDATE = {o: _flops(f"nc_step_cell_update_1d_order{o}") for o in (5, 6)}
 # Executed flops of the face-flux kernel itself (ncu: 2 x FMA + ADD + MUL of
-# the pipe, per face Gauss point, on a 256^2 case whose index space is whole
+# the pipe, scalar and packed two-lane forms, per face Gauss point, on a 256^2 case whose index space is whole
 # 128-item groups, so every point is evaluated exactly once; mean of the four
 # launches of a step; the face-flux flop summary under profiles/).  The
 # kernel uses closed forms where the oracle solves moment systems, so it
 # executes fewer flops than the algorithmic count.
-EXECUTED_FLOPS_PER_FACE_GP = {"mixed": 1686.2, "fp64": 1908.1}
+EXECUTED_FLOPS_PER_FACE_GP = {"mixed": 1567.7, "fp64": 1908.1}
 # DRAM bytes (read + write) per launch of the face-flux kernel: the mean of
 # the four launches of a 1-pass ncu capture at 1024^2 (coefficients 151 MB
 # FP32 / 303 MB FP64, above L2): 202.4 MB mixed, 854.7 MB FP64, scaled to
@@ -507,9 +507,10 @@ def time_3d(B, torch, steps, dev, ffma):
             "workload": "3D 256^3 periodic solenoidal velocity (E(k) ~ k^4 exp(-2(k/4)^2), rms Mach 0.6), mixed precision"}
 
 
-def run_case(n, precision, steps):
+def run_case(n, precision, steps, stage_kernels=0):
     """A small run of the headline workload for ncu captures: the n^2
-    periodic Fourier-mode + shock state, `steps` CFL steps through the C ABI."""
+    periodic Fourier-mode + shock state, `steps` CFL steps through the C ABI
+    (stage_kernels 1: the fused stage kernel)."""
     import numpy as np
     import torch
 
@@ -517,7 +518,7 @@ def run_case(n, precision, steps):
     from paper_2507_20461_gb300 import inputs as I
 
     W, G, h = I.fourier_shocks_2d(n, SEED)
-    s = B.Solver((n, n), bc=B.BC_PERIODIC, precision=precision)
+    s = B.Solver((n, n), bc=B.BC_PERIODIC, precision=precision, stage_kernels=stage_kernels)
     Wd = torch.from_numpy(np.ascontiguousarray(W)).cuda()
     Gd = torch.from_numpy(np.ascontiguousarray(G)).cuda()
     s.set_state(Wd, Gd)
@@ -525,7 +526,7 @@ def run_case(n, precision, steps):
     torch.cuda.synchronize()
     st = s.status()
     s.close()
-    print(f"case n={n} precision={precision} steps={steps} status={st}")
+    print(f"case n={n} precision={precision} steps={steps} stage_kernels={stage_kernels} status={st}")
     return 0 if st == 0 else 1
 
 
@@ -575,6 +576,7 @@ def main():
                     help="profiling case: N^2 cells of the headline IC, --case-steps CFL steps, then exit (no JSON)")
     ap.add_argument("--case-precision", type=int, default=1, choices=[0, 1])
     ap.add_argument("--case-steps", type=int, default=2)
+    ap.add_argument("--case-stage-kernels", type=int, default=0, choices=[0, 1])
     ap.add_argument("--cpu-sample", type=int, default=0, metavar="N",
                     help="only time the oracle on an N^2 sample of the workload and print its JSON")
     ap.add_argument("--cpu-steps", type=int, default=1)
@@ -582,7 +584,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.case:
-        return run_case(args.case, args.case_precision, args.case_steps)
+        return run_case(args.case, args.case_precision, args.case_steps, args.case_stage_kernels)
     if args.cpu_sample:
         print(json.dumps(cpu_baseline(args.cpu_sample, args.cpu_steps)))
         return 0
