@@ -38,9 +38,17 @@
  * terms of the integrals add tau (cF1 D - V) to F, tau cT1 D to Ft and
  * -tau e_t (WTk + WAk) to W(dt/2), with V = rho0 <u psi (T0 + A0)>_0 and
  * D = V - FTk - FAk (FAk, WAk: the two half-space moments of A_l, A_r).
+ *
+ * The FP32 Euler flux evaluates the left and the right Maxwellian together
+ * on lane pairs (lr2.cuh: one packed two-lane instruction for both sides);
+ * the arithmetic of each lane is the scalar code's.
  */
 #pragma once
 #include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "lr2.cuh"
 
 namespace gks {
 
@@ -66,6 +74,19 @@ template <> struct RT<float> {
     __device__ static float abs_(float x) { return fabsf(x); }
 };
 
+/* left/right pairs: the transcendentals per lane */
+template <> struct RT<LR> {
+    __device__ static LR erfc_(LR x) { return LR(erfcf(x.l()), erfcf(x.r())); }
+    __device__ static LR exp_(LR x) { return LR(__expf(x.l()), __expf(x.r())); }
+    __device__ static LR sqrt_(LR x) { return LR(sqrtf(x.l()), sqrtf(x.r())); }
+    __device__ static LR rsqrt_(LR x) { return LR(rsqrtf(x.l()), rsqrtf(x.r())); }
+};
+
+/* x > 0 (every lane of a pair) */
+__device__ __forceinline__ bool positive(double x) { return x > 0.0; }
+__device__ __forceinline__ bool positive(float x) { return x > 0.f; }
+__device__ __forceinline__ bool positive(LR x) { return x.l() > 0.f && x.r() > 0.f; }
+
 /* Primitive description of a Maxwellian: density, velocity, pressure,
  * 1/(2 lambda) = p/rho, lambda = rho/(2p), and 1/rho (each reciprocal taken
  * once per Maxwellian and shared by every moment and slope of it). */
@@ -90,7 +111,7 @@ __device__ __forceinline__ bool to_prim(const R *W, R gm1, Prim<R, M> &P)
     P.i2l = P.p * inv;
     P.lam = R(0.5) / P.i2l;
     P.inv = inv;
-    return (W[0] > R(0)) && (P.p > R(0));
+    return positive(W[0]) && positive(P.p);
 }
 
 /* Moments of a Maxwellian: u-moments (full or half space), full v, w moments,
@@ -111,13 +132,12 @@ __device__ __forceinline__ void full_moments(R U, R i2l, R *m)
     for (int k = 0; k + 2 < N; ++k) m[k + 2] = U * m[k + 1] + R(k + 1) * i2l * m[k];
 }
 
-/* half-space u moments: sign = +1 integrates u > 0, -1 integrates u < 0 */
+/* half-space u moments: s = +1 integrates u > 0, -1 integrates u < 0 */
 template <typename R, int N>
-__device__ __forceinline__ void half_moments(R U, R lam, R i2l, int sign, R *m)
+__device__ __forceinline__ void half_moments(R U, R lam, R i2l, R s, R *m)
 {
     const R isl = RT<R>::rsqrt_(lam); /* 1 / sqrt(lambda) */
     const R x = lam * isl * U;        /* sqrt(lambda) U */
-    const R s = R(sign);
     m[0] = R(0.5) * RT<R>::erfc_(-s * x);
     /* exp(-lambda U^2) / (2 sqrt(pi lambda)) */
     m[1] = U * m[0] + s * R(0.5) * RT<R>::exp_(-x * x) * R(0.56418958354775628) * isl;
@@ -425,18 +445,68 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
     const R Ntot = pick<R>(fp.Ntot, fp.fNtot);
     const R c8N = pick<R>(fp.c8N, fp.fc8N);
     const R K = Ntot - R(M);
-    Prim<R, M> Pl, Pr, P0;
-    if (!to_prim<R, M>(Wl, gm1, Pl) || !to_prim<R, M>(Wr, gm1, Pr)) return false;
-
-    Mom<R, M> Tl, Tr, T0;
-    half_moments<R, 7>(Pl.U[0], Pl.lam, Pl.i2l, +1, Tl.u);
-    half_moments<R, 7>(Pr.U[0], Pr.lam, Pr.i2l, -1, Tr.u);
-    tangential_and_internal<R, M>(Pl, K, Tl);
-    tangential_and_internal<R, M>(Pr, K, Tr);
-
-    /* equilibrium state: kinetic collision of the two half streams */
-    R W0[NV], Fk[NV];
-    {
+    /* The two initial Maxwellians' part: the equilibrium state W0 and its
+     * flux Fk from the kinetic collision of the two half streams, and the
+     * density-weighted slope moments of the two sides, WTs = rho_l <psi T_l>_l
+     * + rho_r <psi T_r>_r and FTs the same with u.  The FP32 Euler flux takes
+     * both sides at once on left/right lane pairs (packed two-lane
+     * instructions); the Navier-Stokes terms below need each side apart. */
+    R W0[NV], Fk[NV], WTs[NV], FTs[NV], pl, pr;
+    Prim<R, M> Pl, Pr;
+    Mom<R, M> Tl, Tr;
+    if constexpr (std::is_same_v<R, float> && !NS) {
+        Prim<LR, M> Q;
+        {
+            LR Wq[NV];
+#pragma unroll
+            for (int b = 0; b < NV; ++b) Wq[b] = LR(Wl[b], Wr[b]);
+            if (!to_prim<LR, M>(Wq, LR(gm1), Q)) return false;
+        }
+        pl = Q.p.l();
+        pr = Q.p.r();
+        Mom<LR, M> T;
+        half_moments<LR, 7>(Q.U[0], Q.lam, Q.i2l, LR(1.f, -1.f), T.u);
+        tangential_and_internal<LR, M>(Q, LR(K), T);
+        {
+            LR e = T.xi[1];
+            if constexpr (M >= 2) e += T.v[2];
+            if constexpr (M >= 3) e += T.w[2];
+            const LR ru0 = Q.rho * T.u[0], ru1 = Q.rho * T.u[1];
+            W0[0] = ru0.sum();
+            W0[1] = ru1.sum();
+            Fk[0] = W0[1];
+            Fk[1] = LR(Q.rho * T.u[2]).sum();
+#pragma unroll
+            for (int i = 1; i < M; ++i) {
+                W0[1 + i] = LR(ru0 * Q.U[i]).sum();
+                Fk[1 + i] = LR(ru1 * Q.U[i]).sum();
+            }
+            W0[M + 1] = R(0.5) * LR(Q.rho * (T.u[2] + T.u[0] * e)).sum();
+            Fk[M + 1] = R(0.5) * LR(Q.rho * (T.u[3] + T.u[1] * e)).sum();
+        }
+        LR sq[M][NV];
+#pragma unroll
+        for (int e = 0; e < M; ++e) {
+            LR rq[NV];
+#pragma unroll
+            for (int b = 0; b < NV; ++b) rq[b] = LR(dWl[e][b], dWr[e][b]) * Q.inv;
+            slope<LR, M>(Q, LR(Ntot), LR(c8N), rq, sq[e]);
+        }
+        LR WT[NV], FT[NV];
+        slope_moments<LR, M>(T, sq, WT, FT);
+#pragma unroll
+        for (int b = 0; b < NV; ++b) {
+            WTs[b] = LR(Q.rho * WT[b]).sum();
+            FTs[b] = LR(Q.rho * FT[b]).sum();
+        }
+    } else {
+        if (!to_prim<R, M>(Wl, gm1, Pl) || !to_prim<R, M>(Wr, gm1, Pr)) return false;
+        pl = Pl.p;
+        pr = Pr.p;
+        half_moments<R, 7>(Pl.U[0], Pl.lam, Pl.i2l, R(1), Tl.u);
+        half_moments<R, 7>(Pr.U[0], Pr.lam, Pr.i2l, R(-1), Tr.u);
+        tangential_and_internal<R, M>(Pl, K, Tl);
+        tangential_and_internal<R, M>(Pr, K, Tr);
         R el = Tl.xi[1], er = Tr.xi[1];
         if constexpr (M >= 2) { el += Tl.v[2]; er += Tr.v[2]; }
         if constexpr (M >= 3) { el += Tl.w[2]; er += Tr.w[2]; }
@@ -451,27 +521,48 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
         }
         W0[M + 1] = R(0.5) * (Pl.rho * (Tl.u[2] + Tl.u[0] * el) + Pr.rho * (Tr.u[2] + Tr.u[0] * er));
         Fk[M + 1] = R(0.5) * (Pl.rho * (Tl.u[3] + Tl.u[1] * el) + Pr.rho * (Tr.u[3] + Tr.u[1] * er));
-    }
-    if (!to_prim<R, M>(W0, gm1, P0)) return false;
-    full_moments<R, 7>(P0.U[0], P0.i2l, T0.u);
-    tangential_and_internal<R, M>(P0, K, T0);
-
-    /* micro-slopes along every face axis */
-    R sl[M][NV], sr[M][NV], s0[M][NV], dW0[M][NV];
-    {
-        const R il = Pl.inv, ir = Pr.inv, i0 = P0.inv;
+        R sl[M][NV], sr[M][NV];
+        const R il = Pl.inv, ir = Pr.inv;
 #pragma unroll
         for (int e = 0; e < M; ++e) {
-            R rl[NV], rr[NV], r0[NV];
+            R rl[NV], rr[NV];
 #pragma unroll
             for (int b = 0; b < NV; ++b) {
                 rl[b] = dWl[e][b] * il;
                 rr[b] = dWr[e][b] * ir;
-                dW0[e][b] = R(0.5) * (dWl[e][b] + dWr[e][b]);
-                r0[b] = dW0[e][b] * i0;
             }
             slope<R, M>(Pl, Ntot, c8N, rl, sl[e]);
             slope<R, M>(Pr, Ntot, c8N, rr, sr[e]);
+        }
+        R FTl[NV], FTr[NV], WTl[NV], WTr[NV];
+        slope_moments<R, M>(Tl, sl, WTl, FTl);
+        slope_moments<R, M>(Tr, sr, WTr, FTr);
+#pragma unroll
+        for (int b = 0; b < NV; ++b) {
+            WTs[b] = Pl.rho * WTl[b] + Pr.rho * WTr[b];
+            FTs[b] = Pl.rho * FTl[b] + Pr.rho * FTr[b];
+        }
+    }
+
+    /* equilibrium state */
+    Prim<R, M> P0;
+    Mom<R, M> T0;
+    if (!to_prim<R, M>(W0, gm1, P0)) return false;
+    full_moments<R, 7>(P0.U[0], P0.i2l, T0.u);
+    tangential_and_internal<R, M>(P0, K, T0);
+
+    /* micro-slopes of the equilibrium along every face axis */
+    R s0[M][NV], dW0[M][NV];
+    {
+        const R i0 = P0.inv;
+#pragma unroll
+        for (int e = 0; e < M; ++e) {
+            R r0[NV];
+#pragma unroll
+            for (int b = 0; b < NV; ++b) {
+                dW0[e][b] = R(0.5) * (dWl[e][b] + dWr[e][b]);
+                r0[b] = dW0[e][b] * i0;
+            }
             slope<R, M>(P0, Ntot, c8N, r0, s0[e]);
         }
     }
@@ -490,14 +581,11 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
         euler_dflux<R, M>(P0, W0, gm1, 0, W0t, FA0);
         euler_flux<R, M>(P0, W0, 0, F0);
     }
-    /* moments carrying the spatial slopes */
-    R FT0[NV], FTl[NV], FTr[NV], WTl[NV], WTr[NV];
+    /* moments carrying the equilibrium's spatial slopes */
+    R FT0[NV];
     slope_moments<R, M>(T0, s0, nullptr, FT0);
-    slope_moments<R, M>(Tl, sl, WTl, FTl);
-    slope_moments<R, M>(Tr, sr, WTr, FTr);
 
     /* collision times and time integrals */
-    const R pl = Pl.p, pr = Pr.p;
     R tn = pick<R>(fp.c1, fp.fc1) * dt + pick<R>(fp.c2, fp.fc2) * RT<R>::abs_(pl - pr) / (pl + pr) * dt;
     /* Navier-Stokes only: the time slopes A of the two initial states, each
      * from its own compatibility condition <psi (sum_e a_e u_e + A) g> = 0,
@@ -558,10 +646,10 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
 #pragma unroll
     for (int b = 0; b < NV; ++b) {
         const R dk = Fk[b] - F0[b];
-        const R dT = P0.rho * FT0[b] - (Pl.rho * FTl[b] + Pr.rho * FTr[b]);
+        const R dT = P0.rho * FT0[b] - FTs[b];
         F[b] = F0[b] + cF1 * dk + cF2 * dT;
         Ft[b] = FA0[b] + cT1 * dk + cT2 * dT;
-        Wh[b] = W0[b] + hdt * (R(1) - eh) * W0t[b] - hdt * eh * (Pl.rho * WTl[b] + Pr.rho * WTr[b]);
+        Wh[b] = W0[b] + hdt * (R(1) - eh) * W0t[b] - hdt * eh * WTs[b];
         if constexpr (NS) {
             /* the tau terms of the time integrals: with V = <u psi (T0 + A0) g0>
              * (the equilibrium's viscous part) and D = V - (left + right
@@ -569,10 +657,10 @@ __device__ __forceinline__ bool gks_point(const FluxParams &fp, R dt, const R *W
              * gains tau cT1 D; the interface state gains -tau e (the two
              * sides' half-space <psi (T + A) g>), since <psi (T0 + A0) g0> = 0 */
             const R V = P0.rho * FT0[b] + FA0[b];
-            const R D = V - (Pl.rho * FTl[b] + Pr.rho * FTr[b]) - FA[b];
+            const R D = V - FTs[b] - FA[b];
             F[b] += tau * (cF1 * D - V);
             Ft[b] += tau * cT1 * D;
-            Wh[b] -= tau * eh * (Pl.rho * WTl[b] + Pr.rho * WTr[b] + WA[b]);
+            Wh[b] -= tau * eh * (WTs[b] + WA[b]);
         }
     }
     return true;
