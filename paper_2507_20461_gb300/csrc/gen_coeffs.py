@@ -58,6 +58,34 @@ def emit_assignments(lines, exprs, names, indent="    "):
     lines.extend(out)
 
 
+def emit_linear(lines, exprs, names, syms, indent="    "):
+    """Emit `name = sum_k K_k * syms[k];` for expressions linear in syms, each
+    coefficient folded (exactly, surds included) into one literal, so that a
+    term costs one fused multiply-add (a product of two literals would cost a
+    multiply more: the compiler may not reassociate floating-point
+    products)."""
+    for n, e in zip(names, exprs):
+        e = sp.expand(e)
+        terms = []
+        for k, sym in enumerate(syms):
+            K = sp.nsimplify(e.coeff(sym))
+            if K == 0:
+                continue
+            kv = float(K)
+            v = f"{sym}"
+            if kv == 1.0:
+                t = v
+            elif kv == -1.0:
+                t = f"-{v}"
+            else:
+                t = f"R({kv!r})*{v}"
+            terms.append(t)
+        rest = sp.expand(e - sum(e.coeff(sym) * sym for sym in syms))
+        assert rest == 0, "expression is not linear in the given symbols"
+        body = " + ".join(terms).replace("+ -", "- ") if terms else "R(0)"
+        lines.append(f"{indent}{n} = {body};")
+
+
 class _Printer(C99CodePrinter):
     def _print_Rational(self, e):
         return lit(e)
@@ -219,7 +247,8 @@ def gen_md(lines, m):
     lines.append(f"__host__ __device__ __forceinline__ void cubic{m}d_fit(const R *__restrict__ d, R *__restrict__ c)")
     lines.append("{")
     dsyms = {d[j]: sp.Symbol(f"d[{j}]") for j in range(nd)}
-    emit_assignments(lines, [ce.xreplace(dsyms) for ce in c_exprs], [f"c[{k}]" for k in range(nc)])
+    emit_linear(lines, [ce.xreplace(dsyms) for ce in c_exprs], [f"c[{k}]" for k in range(nc)],
+                [dsyms[d[j]] for j in range(nd)])
     lines.append("}")
     lines.append("")
 
@@ -270,7 +299,7 @@ def gen_md(lines, m):
                 lines.append("template <typename R>")
                 lines.append(f"__host__ __device__ __forceinline__ void cubic{m}d_eval_d{dd}_s{s}_g{gp}(const R *__restrict__ c, R *__restrict__ out)")
                 lines.append("{")
-                emit_assignments(lines, [ex.xreplace(csyms) for ex in exprs], names)
+                emit_linear(lines, [ex.xreplace(csyms) for ex in exprs], names, [csyms[cs[k]] for k in range(nc)])
                 lines.append("}")
                 lines.append("")
     if m == 2:
