@@ -304,31 +304,46 @@ __device__ __forceinline__ void fused2d_strip(const KP &P, const FusedGeo &geo, 
         if (valid && v == 0) mixed_state_flags<2>(P, w4, status);
     };
 
-    /* prologue: input rows y0 - 2 .. y0 + 1, cubic rows y0 - 1 and y0, the y
-     * faces between them, and input row y0 + 2 */
-    for (int r = y0 - 2; r <= y0 + 1; ++r) load_row(r);
+    /* The sweep, one loop for the whole chunk.  Iteration j: phase A, the
+     * cubics of row j + 1 and the update of row j - 1; phase B, the load of
+     * input row j + 3 and the faces of row j (the x faces of row j and the y
+     * faces between rows j and j + 1).  The first two iterations are the
+     * prologue (j = y0 - 2: cubic row y0 - 1 only; j = y0 - 1: cubic row y0
+     * and the y faces below row y0), the last one the epilogue (j = y1: the
+     * update of row y1 - 1 only).  A cubic row or a face on a chunk's edge
+     * is also computed by the neighbouring chunk, and conservation needs
+     * both results bit-identical: every cubic and every face therefore comes
+     * from the one copy of recon_item / flux_item in this loop.  The row
+     * index and its phase are opaque values, so the compiler can neither
+     * peel the first iterations nor specialise a copy of the code for them. */
+    for (int r = y0 - 2; r <= y0; ++r) load_row(r);
     cp_wait();
     __syncthreads();
-    for (int it = tid; it < 2 * NV * CX; it += NT) recon_item(it < NV * CX ? y0 - 1 : y0, it % (NV * CX));
-    __syncthreads();
-    load_row(y0 + 2);
-    for (int wi = tid >> 5; wi < 2 * T::NYB; wi += NT / 32) flux_item(y0, wi, true);
-    cp_wait();
-    __syncthreads();
-
-    for (int j = y0; j < y1; ++j) {
+#pragma unroll 1
+    for (int jl = y0 - 2; jl <= y1; ++jl) {
+        int j = jl;
+        asm volatile("" : "+r"(j));
+        /* 0: a full row; 1: cubics and the y faces below row y0; 2: cubics
+         * only; 3: the last update only */
+        int phase = j >= y1 ? 3 : (j >= y0 ? 0 : (j == y0 - 1 ? 1 : 2));
+        asm volatile("" : "+r"(phase));
         /* A: cubics of row j + 1; update of row j - 1 */
-        for (int it = tid; it < NV * CX; it += NT) recon_item(j + 1, it);
+        if (phase != 3)
+            for (int it = tid; it < NV * CX; it += NT) recon_item(j + 1, it);
         if (j > y0) update_row(j - 1);
+        if (phase == 3) break;
         __syncthreads();
         /* B: faces of row j; input row j + 3 in flight meanwhile (the slot
          * of row j - 1, which phase A no longer reads) */
         if (j + 1 < y1) load_row(j + 3);
-        for (int wi = tid >> 5; wi < T::NWI; wi += NT / 32) flux_item(j, wi, false);
+        if (phase != 2) {
+            const bool yo = phase == 1;
+            const int nwi = yo ? 2 * T::NYB : T::NWI;
+            for (int wi = tid >> 5; wi < nwi; wi += NT / 32) flux_item(yo ? y0 : j, wi, yo);
+        }
         cp_wait();
         __syncthreads();
     }
-    if (y1 > y0) update_row(y1 - 1);
 }
 
 /* one grid: block (bx, by) sweeps strip bx over the rows' chunk by */
