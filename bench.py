@@ -455,15 +455,18 @@ def time_batch(B, torch, dev, ffma, total_steps=300, warm=3):
             Gd = torch.from_numpy(states[g][1]).to(dev)
             bt.get_state(ids.index(g), Wd, Gd)
             rho[run].append(Wd[0].clone())
+        gstat = bt.grid_status()
         if run == "mixed":
             out = {"value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": steps,
                    "total_steps": total_steps, "grids": 256, "cells": cells, "status": bt.status(),
+                   "nonphysical_grids": {str(ids[k]): v for k, v in enumerate(gstat) if v},
                    "tuning": json.loads(bt.tuning() or "{}"),
                    "roofline": alu_roofline(CELL_UPDATE_2D, cells / (ms * 1e-3), ffma, "whole batched step",
                                             "cell-update", "measured: FP32 FMA probe (scalar or packed, the larger)")}
         elif run == "fp64":
             out["fp64_sampled_ms_per_step"] = ms
             out["fp64_status"] = bt.status()
+            out["fp64_nonphysical_grids"] = {str(ids[k]): v for k, v in enumerate(gstat) if v}
         bt.close()
     spread = [(float((a - b).abs().mean()), float((a - b).abs().max()))
               for a, b in zip(rho["fp64_perturbed"], rho["fp64"])]

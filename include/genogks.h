@@ -326,7 +326,9 @@ typedef struct gks_batch_ctx *gks_batch_t;
 int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs, double gamma, gks_bc_t bc,
                      const gks_opts_t *opts, gks_batch_t *out);
 
-/* State of grid b (layouts as for a single 2D grid).  Host or device memory. */
+/* State of grid b (layouts as for a single 2D grid).  Host or device memory.
+ * set_state clears that grid's status word; get_state copies the state and
+ * then returns GKS_ERR_NONPHYSICAL if that grid's status word is set. */
 int gks_batch_set_state(gks_batch_t b, int grid, const double *W, const double *G, int on_device);
 int gks_batch_get_state(gks_batch_t b, int grid, double *W, double *G, int on_device);
 
@@ -354,8 +356,15 @@ int gks_batch_run(gks_batch_t b, double cfl, int nsteps);
  * size-class key); "" before the first gks_batch_run.  Owned by the handle. */
 const char *gks_batch_tuning(gks_batch_t b);
 
-/* Synchronise and return the status word (as gks_status). */
+/* Synchronise and return the status word (as gks_status): the OR of every
+ * grid's status word. */
 int gks_batch_status(gks_batch_t b);
+/* Synchronise and copy the status word of every grid (as gks_status; 0 for
+ * a grid whose states stayed admissible) to status[0 .. n-1], host memory.
+ * Each grid's word is cleared by gks_batch_set_state of that grid.
+ * GKS_ERR_ARG for a NULL handle or output, or n other than the number of
+ * grids; GKS_ERR_CUDA if the copy fails. */
+int gks_batch_grid_status(gks_batch_t b, int *status, int n);
 
 /* Wait for the batch's work and free everything it owns.  NULL is a no-op. */
 int gks_batch_destroy(gks_batch_t b);

@@ -100,6 +100,7 @@ def lib(build: bool = True):
         "gks_batch_get_state": (C.c_int, [vp, C.c_int, vp, vp, C.c_int]),
         "gks_batch_run": (C.c_int, [vp, C.c_double, C.c_int]),
         "gks_batch_status": (C.c_int, [vp]),
+        "gks_batch_grid_status": (C.c_int, [vp, C.POINTER(C.c_int), C.c_int]),
         "gks_batch_destroy": (C.c_int, [vp]),
         "gks_batch_last_error": (C.c_char_p, [vp]),
         "gks_batch_tuning": (C.c_char_p, [vp]),
@@ -311,6 +312,12 @@ def gks_batch_status(b) -> int:
     return _check(b, lib().gks_batch_status(b), "gks_batch_last_error")
 
 
+def gks_batch_grid_status(b, n: int) -> list:
+    out = (C.c_int * n)()
+    _check(b, lib().gks_batch_grid_status(b, out, n), "gks_batch_last_error")
+    return list(out)
+
+
 def gks_batch_tuning(b) -> str:
     m = lib().gks_batch_tuning(b)
     return m.decode() if m else ""
@@ -344,6 +351,10 @@ class Batch:
 
     def status(self):
         return gks_batch_status(self.h)
+
+    def grid_status(self):
+        """Status word of every grid (0: its states stayed admissible)."""
+        return gks_batch_grid_status(self.h, len(self.nx))
 
     def tuning(self):
         return gks_batch_tuning(self.h)

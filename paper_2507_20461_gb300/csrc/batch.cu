@@ -43,7 +43,8 @@ struct gks_batch_ctx {
     size_t ws_bytes;
     double *dt;
     unsigned long long *smax;
-    int *status;
+    int *status; /* per-grid status words status[g] (OR of the ST_* bits) */
+    int *queue;  /* work counters of the fused stage kernel (one per stage) */
     Tile *tiles[gks::BK_COUNT];
     int ntiles[gks::BK_COUNT];
     LaunchShape shape[gks::BK_COUNT];
@@ -174,7 +175,7 @@ int build_tiles(gks_batch_ctx *b, int k, long tile)
 
 BatchLaunch launch_of(gks_batch_ctx *b, int k)
 {
-    return BatchLaunch{b->dd, b->tiles[k], b->ntiles[k], b->dt, b->smax, b->status, &b->hd[0].P, b->status + 4};
+    return BatchLaunch{b->dd, b->tiles[k], b->ntiles[k], b->dt, b->smax, b->status, &b->hd[0].P, b->queue};
 }
 
 cudaError_t run_class(gks_batch_ctx *b, int k, int stage)
@@ -399,7 +400,7 @@ int tune(gks_batch_ctx *b, double cfl)
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "tuning");
     /* tuning ran stage-1 kernels only; clear the status they may have set */
-    cudaMemset(b->status, 0, sizeof(int));
+    cudaMemset(b->status, 0, sizeof(int) * b->nb);
     b->tuned = 1;
     TuneEntry t;
     for (int k = 0; k < gks::BK_COUNT; ++k) t.shape[k] = b->shape[k];
@@ -466,7 +467,8 @@ int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs,
     const size_t rs = o.precision ? sizeof(float) : sizeof(double);
     b->hd.resize(nbatch);
     b->g_stale.assign(nbatch, 0);
-    size_t off = al(sizeof(double) * nbatch) + al(sizeof(unsigned long long) * nbatch) + al(256);
+    size_t off = al(sizeof(double) * nbatch) + al(sizeof(unsigned long long) * nbatch) + al(sizeof(int) * 8) +
+                 al(sizeof(int) * nbatch);
     std::vector<size_t> base(nbatch);
     for (int g = 0; g < nbatch; ++g) {
         make_kp(b->hd[g].P, nx[g], ny[g], hs[g], gamma, (int)bc, o);
@@ -487,7 +489,8 @@ int gks_batch_create(int nbatch, const int *nx, const int *ny, const double *hs,
     char *w = (char *)b->ws;
     b->dt = (double *)w;
     b->smax = (unsigned long long *)(w + al(sizeof(double) * nbatch));
-    b->status = (int *)(w + al(sizeof(double) * nbatch) + al(sizeof(unsigned long long) * nbatch));
+    b->queue = (int *)(w + al(sizeof(double) * nbatch) + al(sizeof(unsigned long long) * nbatch));
+    b->status = (int *)((char *)b->queue + al(sizeof(int) * 8));
     for (int g = 0; g < nbatch; ++g) {
         GridDesc &D = b->hd[g];
         const gks::KP &P = D.P;
@@ -543,7 +546,7 @@ int gks_batch_set_state(gks_batch_t b, int grid, const double *W, const double *
     if (e == cudaSuccess) e = cudaMemcpyAsync(D.G, G, 2 * n * sizeof(double), k, b->stream);
     if (e == cudaSuccess && b->precision == 1) e = gks::batch_shadow(D, b->stream);
     b->g_stale[grid] = 0;
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status + grid, 0, sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     return e == cudaSuccess ? GKS_OK : bcuda(b, e, "batch set_state");
 }
@@ -567,9 +570,9 @@ int gks_batch_get_state(gks_batch_t b, int grid, double *W, double *G, int on_de
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "batch get_state");
     int st = 0;
-    e = cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(&st, b->status + grid, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return bcuda(b, e, "status read");
-    if (st) return bfail(b, GKS_ERR_NONPHYSICAL, "non-physical state (status bits 0x%x)", st);
+    if (st) return bfail(b, GKS_ERR_NONPHYSICAL, "grid %d: non-physical state (status bits 0x%x)", grid, st);
     return GKS_OK;
 }
 
@@ -619,9 +622,22 @@ int gks_batch_status(gks_batch_t b)
     if (!b) return bfail(nullptr, GKS_ERR_ARG, "NULL handle");
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "stream synchronize");
-    int st = 0;
-    e = cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? st : bcuda(b, e, "status read");
+    std::vector<int> st(b->nb);
+    e = cudaMemcpy(st.data(), b->status, sizeof(int) * b->nb, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "status read");
+    int r = 0;
+    for (int v : st) r |= v;
+    return r;
+}
+
+int gks_batch_grid_status(gks_batch_t b, int *status, int n)
+{
+    if (!b) return bfail(nullptr, GKS_ERR_ARG, "NULL handle");
+    if (!status || n != b->nb) return bfail(b, GKS_ERR_ARG, "status must hold one word per grid (%d)", b->nb);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "stream synchronize");
+    e = cudaMemcpy(status, b->status, sizeof(int) * b->nb, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? GKS_OK : bcuda(b, e, "status read");
 }
 
 const char *gks_batch_tuning(gks_batch_t b) { return b ? b->tuning : ""; }

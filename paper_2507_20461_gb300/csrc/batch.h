@@ -41,7 +41,7 @@ struct BatchLaunch {
     int ntiles;
     double *dt;                 /* per grid */
     unsigned long long *smax;   /* per grid */
-    int *status;
+    int *status;                /* per grid: status[g] */
     const KP *common;           /* host: the scheme constants every grid shares */
     int *queue;                 /* device: work counters of the fused stage kernel (one per stage) */
 };

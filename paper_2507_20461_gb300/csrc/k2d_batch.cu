@@ -86,10 +86,10 @@ __global__ void __launch_bounds__(128, (flux_blocks_per_sm<R, 2, false>())) bk_f
         constexpr bool fsum = sizeof(R) == sizeof(float);
         if (T.kind == 0) {
             for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x)
-                face_flux_item<R, 2, 0, true, false, fsum>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
+                face_flux_item<R, 2, 0, true, false, fsum>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status + T.grid, t);
         } else {
             for (long t = T.begin + threadIdx.x; t < T.end; t += blockDim.x)
-                face_flux_item<R, 2, 1, true, false, fsum>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status, t);
+                face_flux_item<R, 2, 1, true, false, fsum>(g.P, src, (const R *)g.B, dtv, nullptr, (R *)g.ff, status + T.grid, t);
         }
     }
 }
@@ -111,9 +111,9 @@ __global__ void __launch_bounds__(256) bk_update(const GridDesc *__restrict__ gd
         }
         for (long c = T.begin + threadIdx.x; c < T.end; c += blockDim.x) {
             if (stage == 1)
-                update_item<R, 2, 1>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status, c, uc);
+                update_item<R, 2, 1>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status + T.grid, c, uc);
             else
-                update_item<R, 2, 2>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status, c, uc);
+                update_item<R, 2, 2>(g.P, (const R *)g.ff, dtv, g.W, g.G, g.Ws, g.Gs, g.Acc, g.s0, g.s1, status + T.grid, c, uc);
         }
     }
 }
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kStageThreads, kStageMinBlocks)
         float *const h0 = g.s0.hi, *const h1 = g.s1.hi;
         const Shadow s0{h0, h0 + 4 * nc, h0 + 8 * nc}, s1{h1, h1 + 4 * nc, h1 + 8 * nc};
         fused2d_strip<STAGE, false, kStageStrip, kStageThreads>(P, geo, s0, s1, g.W, (float *)g.Acc, dt[T.grid],
-                                                               status, T.kind, (int)T.begin, (int)(T.end - T.begin),
+                                                               status + T.grid, T.kind, (int)T.begin, (int)(T.end - T.begin),
                                                                smem, uc);
     }
 }

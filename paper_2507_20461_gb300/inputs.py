@@ -193,16 +193,15 @@ def batch_sizes(count: int, seed: int, lo: int = 64, hi: int = 1024):
 
 
 # Batched workload (256 grids, sides from batch_sizes(256, 20464)): grid g's
-# four-quadrant IC uses seed 20464 + g + 1000 k, k = BATCH_REDRAWS.get(g, 0),
-# an IC redrawn because a run of it turned non-physical within the workload's
-# 300 steps (the recipe's rule for such seeds).  Grid 87 (82^2): the mixed
-# batch reaches, at the right boundary where the transmissive ghost feeds
-# inflow, a cell with rho = 0.0013 and u = -150 near step 195, and the FP64
-# oracle's step from that state is non-physical too (p = -2.1).  Grid 113
-# (124^2): the mixed path turns non-physical near step 90; the FP64 path
-# runs it through.
+# four-quadrant IC uses seed 20464 + g + 1000 k, k = BATCH_REDRAWS.get(g, 0).
+# The recipe's rule: an IC on which the FP64 path (the oracle's arithmetic)
+# turns non-physical within the workload's 300 steps is redrawn.  Grid 61
+# (64^2): the FP64 batch reaches p <= 0 within its first draw's 300 steps;
+# its redraw runs through in FP64 and in mixed precision.  A grid
+# that only the mixed-precision path turns non-physical is kept and reported
+# (Batch.grid_status), not redrawn.
 BATCH_BASE_SEED = 20464
-BATCH_REDRAWS = {87: 1, 113: 1}
+BATCH_REDRAWS = {61: 1}
 
 
 def batch_seed(g: int, base: int = BATCH_BASE_SEED) -> int:

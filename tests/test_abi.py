@@ -79,6 +79,8 @@ def test_null_handles_are_rejected():
     assert L.gks_status(None) == B.ERR_ARG
     assert L.gks_destroy(None) == B.OK
     assert L.gks_batch_run(None, 0.4, 1) == B.ERR_ARG
+    st = (C.c_int * 4)()
+    assert L.gks_batch_grid_status(None, st, 4) == B.ERR_ARG
 
 
 def test_fast_division_formula():
