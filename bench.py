@@ -76,7 +76,7 @@ NC_CELL_UPDATE = {o: _flops(f"nc_step_cell_update_1d_order{o}") for o in (5, 6)}
 # launches of a step; the face-flux flop summary under profiles/).  The
 # kernel uses closed forms where the oracle solves moment systems, so it
 # executes fewer flops than the algorithmic count.
-EXECUTED_FLOPS_PER_FACE_GP = {"mixed": 1567.7, "fp64": 1908.1}
+EXECUTED_FLOPS_PER_FACE_GP = {"mixed": 1523.8, "fp64": 1853.1}
 # DRAM bytes (read + write) per launch of the face-flux kernel: the mean of
 # the four launches of a 1-pass ncu capture at 1024^2 (coefficients 151 MB
 # FP32 / 303 MB FP64, above L2): 202.4 MB mixed, 854.7 MB FP64, scaled to

@@ -295,6 +295,7 @@ int geno_gks_create_sides(const gks_grid_t *grid, double gamma, int order, const
     c->Gs = (double *)(base + L.Gs);
     c->Acc = (double *)(base + L.Acc);
     c->dt = (double *)(base + L.small);
+    c->updc = (float *)(base + L.small + 16);
     c->smax = (unsigned long long *)(base + L.small + 64);
     c->status = (int *)(base + L.small + 128);
     c->B = base + L.B;
@@ -442,7 +443,7 @@ int gks_flux(gks_handle_t c, double dt, double *out, int on_device)
     if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
     if (!out) return fail(c, GKS_ERR_ARG, "face_flux is NULL");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GKS_ERR_ARG, "dt must be finite and > 0");
-    gks::set_scalar_kernel<<<1, 1, 0, c->stream>>>(c->dt, dt);
+    gks::set_dt_kernel<<<1, 1, 0, c->stream>>>(c->dt, dt, c->shadows ? c->updc : nullptr, gks::updc_cw(c->kp, c->dim));
     cudaError_t e = run_flux(c, 0, false);
     if (e != cudaSuccess) return cuda_fail(c, e, "flux");
     const size_t n = c->ff_elems;
@@ -472,7 +473,7 @@ int gks_step(gks_handle_t c, double dt)
 {
     if (!c) return fail(nullptr, GKS_ERR_ARG, "NULL handle");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, GKS_ERR_ARG, "dt must be finite and > 0");
-    gks::set_scalar_kernel<<<1, 1, 0, c->stream>>>(c->dt, dt);
+    gks::set_dt_kernel<<<1, 1, 0, c->stream>>>(c->dt, dt, c->shadows ? c->updc : nullptr, gks::updc_cw(c->kp, c->dim));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "set dt");
     return two_stages(c);

@@ -28,6 +28,7 @@ struct gks_ctx {
     int g_stale;
     /* device scalars */
     double *dt;
+    float *updc; /* mixed precision: the stage constants of the current dt (UpdC, 10 floats) */
     unsigned long long *smax;
     int *status;
     /* reconstruction coefficients (multi-D) and face quantities, in the

@@ -598,7 +598,20 @@ __device__ __forceinline__ void cell_poly_item(const KP &P, const Src<R> &src, R
      * their ghost signs packed one word per cell (ghost_mask) */
     long cl[2 * M + 1];
     unsigned sm[2 * M + 1];
-    {
+    /* a cell whose whole cross lies inside the grid needs no ghost mapping */
+    bool inner = i >= 1 && i + 1 < P.n[0];
+    if (M >= 2) inner = inner && j >= 1 && j + 1 < P.n[1];
+    if (M >= 3) inner = inner && k >= 1 && k + 1 < P.n[2];
+    if (inner) {
+        const long st[3] = {1, (long)P.n[0], (long)P.n[0] * P.n[1]};
+        cl[0] = ((long)k * P.n[1] + j) * P.n[0] + i;
+        sm[0] = 0;
+#pragma unroll
+        for (int q = 0; q < 2 * M; ++q) {
+            cl[1 + q] = cl[0] + ((q & 1) ? st[q / 2] : -st[q / 2]);
+            sm[1 + q] = 0;
+        }
+    } else {
         int fl[3];
         cl[0] = cell_lin<M>(P, i, j, k, fl);
         sm[0] = ghost_mask<M>(P, fl);
@@ -754,12 +767,14 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
     }
     /* interface states, global axes: st[side][v][c], c = 0 value, 1 + e d/dx_e */
     R st[2][NV][M + 1], cw[2][NV];
+    /* a face inside the grid has two real cells: no ghost mapping, no signs */
+    const bool inner = idx[D] > 0 && idx[D] < P.n[D];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         int ci[3] = {idx[0], idx[1], idx[2]};
         if (side == 0) ci[D] -= 1;
-        int flip[3];
-        const long cl = cell_lin<M>(P, ci[0], ci[1], ci[2], flip);
+        int flip[3] = {0, 0, 0};
+        const long cl = inner ? ((long)ci[2] * P.n[1] + ci[1]) * P.n[0] + ci[0] : cell_lin<M>(P, ci[0], ci[1], ci[2], flip);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             R c[NC], out[M + 1];
@@ -773,7 +788,8 @@ __device__ __forceinline__ void face_flux_item(const KP &P, const Src<R> &src, c
             }
             if (side == 0) CubicEval<R, M, D, 1>::run(g, c, out);
             else CubicEval<R, M, D, 0>::run(g, c, out);
-            const R w0 = R(src.w0(v * P.ncell + cl)) * R(ghost_sign<M>(P, flip, v));
+            R w0 = R(src.w0(v * P.ncell + cl));
+            if (!inner) w0 *= R(ghost_sign<M>(P, flip, v));
             cw[side][v] = w0;
             st[side][v][0] = w0 + out[0];
 #pragma unroll
@@ -1016,6 +1032,27 @@ __device__ __forceinline__ UpdC make_updc(double dt, double cw)
     return u;
 }
 
+/* The stage constants live in a 10-float device buffer, written once per
+ * time step by the kernel that sets dt (so the update kernels neither
+ * recompute them per block in FP64 nor wait on a barrier for them). */
+__device__ __forceinline__ void store_updc(float *p, const UpdC &u)
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        p[2 * k] = u.k[k].hi;
+        p[2 * k + 1] = u.k[k].lo;
+    }
+}
+__device__ __forceinline__ UpdC load_updc(const float *__restrict__ p)
+{
+    UpdC u;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) u.k[k] = F2{p[2 * k], p[2 * k + 1]};
+    return u;
+}
+/* the Gauss-point weight of a face sum over the cell size: 1 / (h NG) */
+__host__ __device__ __forceinline__ double updc_cw(const KP &P, int dim) { return P.ih / (dim == 3 ? 4 : 2); }
+
 /* s + e += x exactly up to the rounding of e (Knuth's TwoSum, FP32 adds
  * only, so nothing can be contracted or reassociated) */
 __device__ __forceinline__ void two_sum_acc(float &s, float &e, float x)
@@ -1207,14 +1244,11 @@ __global__ void __launch_bounds__(256) update_kernel(KP P, const R *__restrict__
                                                     double *__restrict__ W, double *__restrict__ G,
                                                     double *__restrict__ Ws, double *__restrict__ Gs,
                                                     double *__restrict__ Acc, Shadow s0, Shadow s1,
-                                                    int *__restrict__ status)
+                                                    int *__restrict__ status, const float *__restrict__ updc)
 {
-    /* the mixed-precision stage constants, once per block */
-    __shared__ UpdC uc;
-    if constexpr (sizeof(R) == sizeof(float) && M >= 2) {
-        if (threadIdx.x == 0) uc = make_updc(dtp[0], P.ih / ((M == 2) ? 2 : 4));
-        __syncthreads();
-    }
+    /* the mixed-precision stage constants of this time step (FP64 path: unused) */
+    UpdC uc;
+    if constexpr (sizeof(R) == sizeof(float) && M >= 2) uc = load_updc(updc);
     const long cell = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell < P.ncell) update_item<R, M, STAGE>(P, ff, dtp[0], W, G, Ws, Gs, Acc, s0, s1, status, cell, uc);
 }
@@ -1298,7 +1332,7 @@ __global__ void wavespeed_kernel(KP P, const T *__restrict__ W, unsigned long lo
  * cfl h^2 / (2 (m - 1) nu_max), nu_max = mu max(1 / rho) (Sec. 6; the factor
  * 2 (m - 1) is taken as 2 in 1D) */
 static __global__ void dt_from_speed_kernel(const unsigned long long *__restrict__ smax, double cfl_h, double visc,
-                                            double *__restrict__ dtp)
+                                            double *__restrict__ dtp, float *__restrict__ updc, double cw)
 {
     const double s = __longlong_as_double((long long)smax[0]);
     double dt = cfl_h / s;
@@ -1307,8 +1341,14 @@ static __global__ void dt_from_speed_kernel(const unsigned long long *__restrict
         dt = fmin(dt, cfl_h / nu);
     }
     dtp[0] = dt;
+    if (updc) store_updc(updc, make_updc(dt, cw));
 }
 
-static __global__ void set_scalar_kernel(double *__restrict__ p, double v) { p[0] = v; }
+/* a time step given by the caller (and, with updc, its stage constants) */
+static __global__ void set_dt_kernel(double *__restrict__ dtp, double dt, float *__restrict__ updc, double cw)
+{
+    dtp[0] = dt;
+    if (updc) store_updc(updc, make_updc(dt, cw));
+}
 
 } // namespace gks

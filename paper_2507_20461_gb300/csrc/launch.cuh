@@ -86,10 +86,10 @@ template <typename R, int M> static cudaError_t update_impl(gks_ctx *c, int stag
     ProfScope ps(c, GKS_KC_UPDATE);
     if (stage == 1)
         update_kernel<R, M, 1><<<nb, 256, 0, c->stream>>>(P, ff, c->dt, c->W, c->G, c->Ws, c->Gs, c->Acc, c->s0, c->s1,
-                                                          c->status);
+                                                          c->status, c->updc);
     else
         update_kernel<R, M, 2><<<nb, 256, 0, c->stream>>>(P, ff, c->dt, c->W, c->G, c->Ws, c->Gs, c->Acc, c->s0, c->s1,
-                                                          c->status);
+                                                          c->status, c->updc);
     return cudaGetLastError();
 }
 
@@ -115,7 +115,8 @@ template <int M> cudaError_t launch_wavespeed(gks_ctx *c, double cfl)
         /* viscous limit cfl h^2 / (2 (m - 1) nu): passed as the factor
          * 2 (m - 1) mu / h that turns max(1 / rho) into the rate cfl h / dt */
         const double visc = c->kp.fp.mu > 0.0 ? 2.0 * (M > 1 ? M - 1 : 1) * c->kp.fp.mu / c->h : 0.0;
-        dt_from_speed_kernel<<<1, 1, 0, c->stream>>>(c->smax, cfl * c->h, visc, c->dt);
+        dt_from_speed_kernel<<<1, 1, 0, c->stream>>>(c->smax, cfl * c->h, visc, c->dt, c->shadows ? c->updc : nullptr,
+                                                     updc_cw(c->kp, M));
     }
     return cudaGetLastError();
 }

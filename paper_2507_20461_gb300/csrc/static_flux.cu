@@ -121,7 +121,7 @@ extern "C" int gks_flux_2d_static(int nx, int ny, double h, double gamma, gks_bc
     /* the status word must start at zero; the coefficients are fully rewritten */
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e == cudaSuccess) {
-        gks::set_scalar_kernel<<<1, 1, 0, s>>>(dtp, dt);
+        gks::set_dt_kernel<<<1, 1, 0, s>>>(dtp, dt, nullptr, 0.0);
         const gks::Src<double> src{W, G};
         gks::face_flux_prepare<double, 2, 0, true>();
         gks::face_flux_prepare<double, 2, 1, true>();
