@@ -79,10 +79,10 @@ NC_CELL_UPDATE = {o: _flops(f"nc_step_cell_update_1d_order{o}") for o in (5, 6)}
 EXECUTED_FLOPS_PER_FACE_GP = {"mixed": 1523.8, "fp64": 1853.1}
 # DRAM bytes (read + write) per launch of the face-flux kernel: the mean of
 # the four launches of a 1-pass ncu capture at 1024^2 (coefficients 151 MB
-# FP32 / 303 MB FP64, above L2): 202.4 MB mixed, 854.7 MB FP64, scaled to
+# FP32 / 303 MB FP64, above L2): 200.5 MB mixed, 854.8 MB FP64, scaled to
 # the 2048^2 launch by the Gauss points it processes.
-TRAFFIC_PER_FLUX_LAUNCH = {"mixed": 202.43e6 * (2049 * 2048) / (1025 * 1024),
-                           "fp64": 854.69e6 * (2049 * 2048) / (1025 * 1024)}
+TRAFFIC_PER_FLUX_LAUNCH = {"mixed": 200.51e6 * (2049 * 2048) / (1025 * 1024),
+                           "fp64": 854.85e6 * (2049 * 2048) / (1025 * 1024)}
 # Algorithmic HBM bytes per cell-update of the whole step (FP64 state,
 # stage buffers, accumulator), 2D: 60 doubles.
 BYTES_PER_CELL_UPDATE = 480.0

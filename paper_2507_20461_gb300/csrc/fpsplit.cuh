@@ -25,8 +25,10 @@
 
 #ifdef __CUDACC__
 #define GKS_HD __host__ __device__ __forceinline__
+#define GKS_HD_COLD static __host__ __device__ __noinline__
 #else
 #define GKS_HD inline
+#define GKS_HD_COLD static inline
 #endif
 
 namespace gks {
@@ -78,6 +80,16 @@ constexpr uint32_t kRebias = 1023 - 127;
 
 } // namespace fps
 
+/* The hardware conversions, for the values outside the fast ranges: behind a
+ * call, so that the compiler cannot if-convert them into every element's
+ * instruction stream (they issue to the FP64 pipe). */
+GKS_HD_COLD double widen_hw(float x) { return (double)x; }
+GKS_HD_COLD void split_hw(double w, float &h, float &l)
+{
+    h = (float)w;
+    l = (float)(w - (double)h);
+}
+
 /* (double)x.  A normal float's 8-bit exponent and 23-bit fraction move into
  * the 11-bit exponent (rebased) and the top of the 52-bit fraction; zeros
  * keep their sign.  Subnormals, infinities and NaNs go to the hardware. */
@@ -85,7 +97,7 @@ GKS_HD double widen(float x)
 {
     const uint32_t u = fps::fbits(x);
     const uint32_t a = u & 0x7fffffffu;
-    if (a - 0x00800000u >= 0x7f000000u && a != 0) return (double)x;
+    if (a - 0x00800000u >= 0x7f000000u && a != 0) return widen_hw(x);
     const uint32_t hi = (u & 0x80000000u) | (a ? (a >> 3) + (fps::kRebias << 20) : 0u);
     return fps::bitsd(((uint64_t)hi << 32) | (uint64_t)(u << 29));
 }
@@ -117,8 +129,7 @@ GKS_HD void split(double w, float &h, float &l)
         l = 0.f;
         return;
     }
-    h = (float)w;
-    l = (float)(w - (double)h);
+    split_hw(w, h, l);
 }
 
 } // namespace gks
