@@ -3,7 +3,7 @@
 The oracle's C source is compiled once more as C++ with every
 floating-point type replaced by the counting scalar of ``opcount.hpp``
 (common subexpressions shared, constants folded; see that header), together
-with the driver ``opcount_main.cpp``.  The counts are the algorithmic work of
+with the main program ``opcount_main.cpp``.  The counts are the algorithmic work of
 the method as the oracle states it: flops = add/sub + mul + div (a fused
 multiply-add counts 2), and the transcendentals exp, erfc, sqrt, tanh one
 each, reported apart.  Used by tests and by the script that records the
@@ -30,7 +30,7 @@ def _inputs():
 
 
 def build(force: bool = False) -> str:
-    """Translate the oracle to the counting scalar and compile the driver."""
+    """Translate the oracle to the counting scalar and compile the main program."""
     os.makedirs(_BUILD, exist_ok=True)
     if not force and os.path.exists(_EXE) and os.path.getmtime(_EXE) >= max(os.path.getmtime(f) for f in _inputs()):
         return _EXE

@@ -1,5 +1,5 @@
 /*
- * Driver of the op-counting build of the oracle (TEST INFRASTRUCTURE ONLY).
+ * Main program of the op-counting build of the oracle (TEST INFRASTRUCTURE ONLY).
  * oracle/opcount.py translates geno_gks_oracle.c to the counting scalar
  * (opcount.hpp) as oracle_ocn.inc and compiles this file with it.
  *
