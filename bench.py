@@ -510,6 +510,30 @@ def time_3d(B, torch, steps, dev, ffma):
             "workload": "3D 256^3 periodic solenoidal velocity (E(k) ~ k^4 exp(-2(k/4)^2), rms Mach 0.6), mixed precision"}
 
 
+def run_case_batch(count, steps):
+    """A small run of the batched workload for ncu captures: `count` grids of
+    the four-quadrant recipe (sides log-uniform in [64, 1024]), mixed
+    precision, `steps` CFL steps (the first call tunes and records the graph)."""
+    import numpy as np
+    import torch
+
+    from paper_2507_20461_gb300 import binding as B
+    from paper_2507_20461_gb300 import inputs as I
+
+    sides = I.batch_sizes(count, seed=I.BATCH_BASE_SEED)
+    bt = B.Batch(sides, sides, [1.0 / n for n in sides], bc=B.BC_TRANSMISSIVE, precision=1)
+    for g, n in enumerate(sides):
+        W, G, h = I.quadrants_2d(n, seed=I.batch_seed(g))
+        bt.set_state(g, torch.from_numpy(np.ascontiguousarray(W)).cuda(), torch.from_numpy(np.ascontiguousarray(G)).cuda())
+    bt.run(CFL, 1)
+    bt.run(CFL, steps)
+    torch.cuda.synchronize()
+    st = bt.status()
+    bt.close()
+    print(f"case batch grids={count} cells={sum(n * n for n in sides)} steps={steps + 1} status={st}")
+    return 0 if st == 0 else 1
+
+
 def run_case(n, precision, steps, stage_kernels=0):
     """A small run of the headline workload for ncu captures: the n^2
     periodic Fourier-mode + shock state, `steps` CFL steps through the C ABI
@@ -580,6 +604,8 @@ def main():
     ap.add_argument("--case-precision", type=int, default=1, choices=[0, 1])
     ap.add_argument("--case-steps", type=int, default=2)
     ap.add_argument("--case-stage-kernels", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--case-batch", type=int, default=0, metavar="G",
+                    help="ncu helper: a small batch of G grids of the batched recipe, then exit")
     ap.add_argument("--cpu-sample", type=int, default=0, metavar="N",
                     help="only time the oracle on an N^2 sample of the workload and print its JSON")
     ap.add_argument("--cpu-steps", type=int, default=1)
@@ -588,6 +614,8 @@ def main():
         return run_reference(args)
     if args.case:
         return run_case(args.case, args.case_precision, args.case_steps, args.case_stage_kernels)
+    if args.case_batch:
+        return run_case_batch(args.case_batch, args.case_steps)
     if args.cpu_sample:
         print(json.dumps(cpu_baseline(args.cpu_sample, args.cpu_steps)))
         return 0
