@@ -86,8 +86,11 @@ typedef enum {
 } gks_bc_t;
 
 typedef struct {
-    int precision;    /* 0: FP64 throughout; 1: reconstruction and flux in FP32,
-                         averages, gradients and stage combination in FP64       */
+    int precision;    /* 0: FP64 throughout; 1: reconstruction and flux in FP32;
+                         the averages accumulated exactly (double-float face sums,
+                         FP64 state); the averaged gradients, recomputed each
+                         stage from the FP32 interface states (Gauss theorem),
+                         in FP32 and widened to FP64 when read                   */
     int limiter;      /* 0: GENO; 1: linear scheme (chi = 1); 2: WENO-Z weights
                          (Eq. wgt-WENO-Z); 3: TENO weights (Eq. wgt-TENO-1,
                          Eq. wgt-TENO-2).  2 and 3 use GENO's candidates (the
