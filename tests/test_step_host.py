@@ -72,3 +72,28 @@ def test_host_step_matches_oracle(exe, oracle, n, bc, lim):
     for a in range(m):
         for v in range(m + 2):
             assert np.abs(Gg[a, v] - Go[a, v]).sum() <= 1e-11 * (np.abs(Go[a, v]).sum() + np.abs(Go).sum() * 1e-3)
+
+
+@pytest.mark.parametrize("seed", [3, 11])
+def test_host_step_quadrants_matches_oracle(exe, oracle, seed):
+    """The four-quadrant Riemann state of the batched workload (jumps: GENO's
+    weights far from linear, the admissibility fallback in play), 20^2,
+    transmissive: the host step against the oracle's at the same bar."""
+    from paper_2507_20461_gb300 import inputs as I
+
+    n = 20
+    W, G, h = I.quadrants_2d(n, seed=seed)
+    cfg = oracle.make_cfg(2, (n, n), h, bc=1)
+    dt = 0.4 * h / oracle.max_wavespeed(cfg, W)
+    text = repr(dt) + "\n" + " ".join(repr(float(v)) for v in W.ravel()) + "\n" + \
+        " ".join(repr(float(v)) for v in G.ravel()) + "\n"
+    r = subprocess.run([exe, "2", str(n), str(n), "1", repr(h), "1", "0"], input=text, capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.strip().splitlines()
+    Wg = np.array([float(t) for t in lines[0].split()]).reshape(W.shape)
+    assert int(lines[2]) == 0
+    Wo, Go = W.copy(), G.copy()
+    assert oracle.step(cfg, dt, Wo, Go) == 0
+    for v in range(4):
+        assert np.abs(Wg[v] - Wo[v]).sum() <= 1e-12 * np.abs(Wo[v]).sum(), v
