@@ -712,10 +712,10 @@ def test_mixed_smooth_flow_tracks_fp64_sensitivity(sk):
     which matches the oracle to 1e-12 per step), and after 300 steps stays
     within 3x of the FP64 path's own divergence from an input perturbed by a
     relative 2^-24 (measured 1.3x).  Even this flow amplifies rounding-level
-    differences (GENO's path function where the indicators' ratios are far
-    from 1): the perturbed FP64 run differs by 3e-8 at step 20 and by 8e-5
-    at step 300, so an absolute bar at that horizon would measure the flow,
-    not the precision split."""
+    differences (the linear scheme, chi = 1, amplifies them more than GENO):
+    the perturbed FP64 run differs by 3e-8 at step 20 and by 8e-5 at step
+    300, so an absolute bar at that horizon would measure the scheme's
+    sensitivity, not the precision split."""
     n = 256
     W, G, h = I.fourier_shocks_2d(n, seed=20463, nshocks=0, drift=(0.5, 0.25))
     cfg = O.make_cfg(2, (n, n), h, bc=0)
