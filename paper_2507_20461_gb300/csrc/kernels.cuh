@@ -1033,8 +1033,10 @@ __device__ __forceinline__ UpdC make_updc(double dt, double cw)
 }
 
 /* The stage constants live in a 10-float device buffer, written once per
- * time step by the kernel that sets dt (so the update kernels neither
- * recompute them per block in FP64 nor wait on a barrier for them). */
+ * time step by the kernel that sets dt, so the update kernel (one cell per
+ * thread) neither recomputes them per block in FP64 nor waits on a barrier
+ * for them.  The fused stage kernels compute them once per strip, which
+ * their rows amortise. */
 __device__ __forceinline__ void store_updc(float *p, const UpdC &u)
 {
 #pragma unroll
