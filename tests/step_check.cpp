@@ -2,7 +2,8 @@
 // face_flux_item, update_item, the per-item functions of the GPU kernels) for
 // the CPU tests, through the test-only CUDA stand-in in tests/hostshim: the
 // two stages of one step run item by item in plain loops.  Arguments:
-// M n0 n1 n2 h bc limiter.  stdin: dt, W[nv][cells], G[M][nv][cells].
+// M n0 n1 n2 h bc limiter [mu] (mu > 0: the Navier-Stokes flux).  stdin: dt,
+// W[nv][cells], G[M][nv][cells].
 // stdout: W then G after the step (one line each), then the status word.
 #include <cmath>
 #include <cstdio>
@@ -12,7 +13,7 @@
 
 #include "kernels.cuh"
 
-template <int M> static int step(gks::KP &P, double dt, std::vector<double> &W, std::vector<double> &G)
+template <int M, bool NS> static int step(gks::KP &P, double dt, std::vector<double> &W, std::vector<double> &G)
 {
     constexpr int NV = M + 2, NC = gks::Cubic<double, M>::NC, NG = (M == 2) ? 2 : 4;
     const long nc = P.ncell;
@@ -25,12 +26,12 @@ template <int M> static int step(gks::KP &P, double dt, std::vector<double> &W, 
         const gks::Src<double> src{stage == 1 ? W.data() : Ws.data(), stage == 1 ? G.data() : Gs.data()};
         for (long t = 0; t < P.next; ++t) gks::cell_poly_item<double, M>(P, src, B.data(), t);
         for (long t = 0; t < P.nface[0] * NG; ++t)
-            gks::face_flux_item<double, M, 0, true>(P, src, B.data(), dt, nullptr, ff.data(), &status, t);
+            gks::face_flux_item<double, M, 0, true, NS>(P, src, B.data(), dt, nullptr, ff.data(), &status, t);
         for (long t = 0; t < P.nface[1] * NG; ++t)
-            gks::face_flux_item<double, M, 1, true>(P, src, B.data(), dt, nullptr, ff.data(), &status, t);
+            gks::face_flux_item<double, M, 1, true, NS>(P, src, B.data(), dt, nullptr, ff.data(), &status, t);
         if constexpr (M == 3)
             for (long t = 0; t < P.nface[2] * NG; ++t)
-                gks::face_flux_item<double, M, 2, true>(P, src, B.data(), dt, nullptr, ff.data(), &status, t);
+                gks::face_flux_item<double, M, 2, true, NS>(P, src, B.data(), dt, nullptr, ff.data(), &status, t);
         for (long c = 0; c < nc; ++c) {
             if (stage == 1)
                 gks::update_item<double, M, 1>(P, ff.data(), dt, W.data(), G.data(), Ws.data(), Gs.data(), Acc.data(),
@@ -46,6 +47,7 @@ template <int M> static int step(gks::KP &P, double dt, std::vector<double> &W, 
 int main(int argc, char **argv)
 {
     if (argc < 8) return 2;
+    const double mu = argc > 8 ? std::atof(argv[8]) : 0.0;
     const int m = std::atoi(argv[1]);
     const int n[3] = {std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4])};
     const double h = std::atof(argv[5]);
@@ -84,6 +86,7 @@ int main(int argc, char **argv)
     P.fp.gamma = 1.4;
     P.fp.c1 = 0.05;
     P.fp.c2 = 1.0;
+    P.fp.mu = mu;
     gks::finalize_kp(P);
     double dt;
     if (std::scanf("%lf", &dt) != 1) return 2;
@@ -92,7 +95,8 @@ int main(int argc, char **argv)
         if (std::scanf("%lf", &x) != 1) return 2;
     for (double &x : G)
         if (std::scanf("%lf", &x) != 1) return 2;
-    const int st = m == 2 ? step<2>(P, dt, W, G) : step<3>(P, dt, W, G);
+    const int st = m == 2 ? (mu > 0 ? step<2, true>(P, dt, W, G) : step<2, false>(P, dt, W, G))
+                          : (mu > 0 ? step<3, true>(P, dt, W, G) : step<3, false>(P, dt, W, G));
     for (size_t i = 0; i < W.size(); ++i) std::printf("%.17g%c", W[i], i + 1 < W.size() ? ' ' : '\n');
     for (size_t i = 0; i < G.size(); ++i) std::printf("%.17g%c", G[i], i + 1 < G.size() ? ' ' : '\n');
     std::printf("%d\n", st);

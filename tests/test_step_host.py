@@ -97,3 +97,30 @@ def test_host_step_quadrants_matches_oracle(exe, oracle, seed):
     assert oracle.step(cfg, dt, Wo, Go) == 0
     for v in range(4):
         assert np.abs(Wg[v] - Wo[v]).sum() <= 1e-12 * np.abs(Wo[v]).sum(), v
+
+
+@pytest.mark.parametrize("n,bc", [((12, 10), 0), ((10, 9), 3), ((6, 5, 4), 1)])
+def test_host_navier_stokes_step_matches_oracle(exe, oracle, n, bc):
+    """The Navier-Stokes flux (physical collision time mu / p0 added to the
+    numerical one) through the same host-built step, against the oracle's
+    viscous step (tau_mode 2): periodic, no-slip walls and 3D."""
+    m = len(n)
+    mu = 0.01
+    W, G, h, shape = _state(n, 31 * sum(n) + bc)
+    Wf, Gf = W.reshape((m + 2,) + shape), G.reshape((m, m + 2) + shape)
+    cfg = oracle.make_cfg(m, n, h, bc=bc, tau_mode=2, mu=mu)
+    dt = 0.3 * h / oracle.max_wavespeed(cfg, np.ascontiguousarray(Wf))
+    text = repr(dt) + "\n" + " ".join(repr(float(v)) for v in W.ravel()) + "\n" + \
+        " ".join(repr(float(v)) for v in G.ravel()) + "\n"
+    n3 = list(n) + [1] * (3 - m)
+    r = subprocess.run([exe, str(m), *map(str, n3), repr(h), str(bc), "0", repr(mu)], input=text,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.strip().splitlines()
+    Wg = np.array([float(t) for t in lines[0].split()]).reshape(W.shape)
+    assert int(lines[2]) == 0
+    Wo, Go = np.ascontiguousarray(Wf.copy()), np.ascontiguousarray(Gf.copy())
+    assert oracle.step(cfg, dt, Wo, Go) == 0
+    Wo = Wo.reshape(W.shape)
+    for v in range(m + 2):
+        assert np.abs(Wg[v] - Wo[v]).sum() <= 1e-12 * np.abs(Wo[v]).sum(), v
