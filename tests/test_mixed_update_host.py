@@ -1,5 +1,5 @@
 """The library's mixed-precision stage update (csrc/kernels.cuh,
-update_item<float, 2, S>), compiled for the CPU through the test-only CUDA
+update_item<float, M, S>, 2D and 3D), compiled for the CPU through the test-only CUDA
 stand-in of tests/hostshim, on random FP32 face sums, checked against exact
 rational arithmetic of the two-stage update (stage 1: W* = W + k0 S(F) +
 k1 S(Ft), Acc = k2 S(F) + k3 S(Ft); stage 2: W^{n+1} = W + Acc + k4 S(Ft*),
@@ -36,23 +36,29 @@ def exe(tmp_path_factory):
     return out
 
 
-def test_mixed_update_matches_exact_arithmetic(exe):
-    nx, ny, h, dt = 7, 5, 1.0 / 64, 2.3e-3
-    nc = nx * ny
-    fx, fy = (nx + 1) * ny, nx * (ny + 1)
-    nf = fx + fy
-    rng = np.random.default_rng(12)
-    W = 1.0 + 0.3 * rng.normal(size=(4, nc))
-    W[1:3] *= 0.1
+@pytest.mark.parametrize("n", [(7, 5), (4, 5, 3)])
+def test_mixed_update_matches_exact_arithmetic(exe, n):
+    m = len(n)
+    nv, ng = m + 2, (2 if m == 2 else 4)
+    h, dt = 1.0 / 64, 2.3e-3
+    nx, ny = n[0], n[1]
+    nz = n[2] if m == 3 else 1
+    nc = nx * ny * nz
+    nfd = [(nx + (d == 0)) * (ny + (d == 1)) * (nz + (d == 2)) for d in range(m)]
+    foff = [sum(nfd[:d]) for d in range(m)]
+    nf = sum(nfd)
+    rng = np.random.default_rng(12 + m)
+    W = 1.0 + 0.3 * rng.normal(size=(nv, nc))
+    W[1:m + 1] *= 0.1
 
     def faces():
-        mag = 10.0 ** rng.uniform(-2, 2, size=(3, 4, nf))
-        return (rng.uniform(-1, 1, size=(3, 4, nf)) * mag).astype(np.float32)
+        mag = 10.0 ** rng.uniform(-2, 2, size=(3, nv, nf))
+        return (rng.uniform(-1, 1, size=(3, nv, nf)) * mag).astype(np.float32)
 
     ff1, ff2 = faces(), faces()
     text = "\n".join(" ".join(repr(float(x)) for x in a.ravel()) for a in (W, ff1, ff2)) + "\n"
-    r = subprocess.run([exe, str(nx), str(ny), repr(h), repr(dt)], input=text, capture_output=True, text=True,
-                       timeout=60)
+    r = subprocess.run([exe, str(nx), str(ny), str(n[2] if m == 3 else 0), repr(h), repr(dt)], input=text,
+                       capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stderr
     rows = r.stdout.strip().splitlines()
     arr = [[Fr(float.fromhex(t)) for t in ln.split()] for ln in rows[:8]]
@@ -60,40 +66,48 @@ def test_mixed_update_matches_exact_arithmetic(exe):
     # (the random face sums make some states non-physical, so the status
     # word is set; the arithmetic is what is checked here)
 
-    cw = 1.0 / h / 2  # 1 / (h NG), NG = 2 Gauss points per face in 2D
+    cw = 1.0 / h / ng  # 1 / (h NG)
     k = [Fr(-0.5 * dt * cw), Fr(-0.125 * dt * dt * cw), Fr(-dt * cw), Fr(-dt * dt / 6.0 * cw), Fr(-dt * dt / 3.0 * cw)]
 
-    def face(ff, q, v, d, i, j, plus):
-        if d == 0:
-            return Fr(float(ff[q, v, j * (nx + 1) + i + plus]))
-        return Fr(float(ff[q, v, fx + (j + plus) * nx + i]))
+    def face(ff, q, v, d, idx, plus):
+        e = [nx + (d == 0), ny + (d == 1), nz + (d == 2)]
+        c = list(idx)
+        c[d] += plus
+        return Fr(float(ff[q, v, foff[d] + (c[2] * e[1] + c[1]) * e[0] + c[0]]))
 
-    def S(ff, q, v, i, j):
-        return sum(face(ff, q, v, d, i, j, 1) - face(ff, q, v, d, i, j, 0) for d in (0, 1))
+    def S(ff, q, v, idx):
+        return sum(face(ff, q, v, d, idx, 1) - face(ff, q, v, d, idx, 0) for d in range(m))
+
+    def mag(ff, q, v, idx):
+        """sum of the face values' magnitudes: the scale of the error term of
+        an exact (double-float) face sum, whatever the cancellation"""
+        return sum(abs(face(ff, q, v, d, idx, 1)) + abs(face(ff, q, v, d, idx, 0)) for d in range(m))
 
     e45 = Fr(1, 2**45)
-    for v in range(4):
-        for j in range(ny):
-            for i in range(nx):
-                c = j * nx + i
-                w = Fr(float(W[v, c]))
-                sF, sT = S(ff1, 0, v, i, j), S(ff1, 1, v, i, j)
-                d1 = k[0] * sF + k[1] * sT
-                ws = w + d1
-                assert abs(h1[v * nc + c] + l1[v * nc + c] - ws) <= e45 * (abs(w) + abs(k[0] * sF) + abs(k[1] * sT))
-                A = k[2] * sF + k[3] * sT
-                a = acc[v * nc + c] + acc[(4 + v) * nc + c]
-                assert abs(a - A) <= e45 * (abs(k[2] * sF) + abs(k[3] * sT))
-                for d in (0, 1):
-                    gd = (face(ff1, 2, v, d, i, j, 1) - face(ff1, 2, v, d, i, j, 0)) * Fr(float(np.float32(cw)))
-                    got = g1[(d * 4 + v) * nc + c]
-                    assert abs(got - gd) <= Fr(1, 2**21) * abs(gd) + Fr(1, 2**100)
-                # stage 2 from the carried accumulator
-                sT2 = S(ff2, 1, v, i, j)
-                wn = w + a + k[4] * sT2
-                got = Wn[v * nc + c]
-                assert abs(got - wn) <= Fr(1, 2**51) * abs(wn) + e45 * (abs(a) + abs(k[4] * sT2))
-                # the new shadow is the exact split of the new FP64 state
-                hh = np.float32(float(got))
-                assert h0[v * nc + c] == Fr(float(hh))
-                assert l0[v * nc + c] == Fr(float(np.float32(float(got) - float(hh))))
+    for v in range(nv):
+        for kz in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    idx = (i, j, kz)
+                    c = (kz * ny + j) * nx + i
+                    w = Fr(float(W[v, c]))
+                    sF, sT = S(ff1, 0, v, idx), S(ff1, 1, v, idx)
+                    mF, mT = mag(ff1, 0, v, idx), mag(ff1, 1, v, idx)
+                    ws = w + k[0] * sF + k[1] * sT
+                    assert abs(h1[v * nc + c] + l1[v * nc + c] - ws) <= e45 * (abs(w) + abs(k[0]) * mF + abs(k[1]) * mT)
+                    A = k[2] * sF + k[3] * sT
+                    a = acc[v * nc + c] + acc[(nv + v) * nc + c]
+                    assert abs(a - A) <= e45 * (abs(k[2]) * mF + abs(k[3]) * mT)
+                    for d in range(m):
+                        gd = (face(ff1, 2, v, d, idx, 1) - face(ff1, 2, v, d, idx, 0)) * Fr(float(np.float32(cw)))
+                        got = g1[(d * nv + v) * nc + c]
+                        assert abs(got - gd) <= Fr(1, 2**21) * abs(gd) + Fr(1, 2**100)
+                    # stage 2 from the carried accumulator
+                    sT2 = S(ff2, 1, v, idx)
+                    wn = w + a + k[4] * sT2
+                    got = Wn[v * nc + c]
+                    assert abs(got - wn) <= Fr(1, 2**51) * abs(wn) + e45 * (abs(a) + abs(k[4]) * mag(ff2, 1, v, idx))
+                    # the new shadow is the exact split of the new FP64 state
+                    hh = np.float32(float(got))
+                    assert h0[v * nc + c] == Fr(float(hh))
+                    assert l0[v * nc + c] == Fr(float(np.float32(float(got) - float(hh))))
